@@ -1,0 +1,324 @@
+"""FP64 CPU oracle for the FastNeRF cached rendering path (ctypes wrapper of oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the
+benchmark's CPU-baseline leg. The renderer package never imports it, and it
+shares no code with the renderer. What each function follows in the paper is
+stated in oracle.c.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+FP32, FP16, FP8 = 0, 1, 2
+ACT_SIGMOID, ACT_IDENTITY = 0, 1
+
+FIELD_FN = ctypes.CFUNCTYPE(None, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
+
+
+class _Cache(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("D", ctypes.c_int32), ("l", ctypes.c_int32),
+                ("bmin", ctypes.c_float * 3), ("bmax", ctypes.c_float * 3),
+                ("pos_prec", ctypes.c_int32), ("dir_prec", ctypes.c_int32),
+                ("sigma", ctypes.c_void_p), ("uvw", ctypes.c_void_p), ("beta", ctypes.c_void_p),
+                ("scales", ctypes.c_void_p), ("field", ctypes.c_void_p), ("field_user", ctypes.c_void_p)]
+
+
+class _Camera(ctypes.Structure):
+    _fields_ = [("c2w", ctypes.c_float * 12), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("W", ctypes.c_int32), ("H", ctypes.c_int32)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("t_near", ctypes.c_float), ("t_far", ctypes.c_float),
+                ("t_thr", ctypes.c_float), ("bg", ctypes.c_float * 3), ("act", ctypes.c_int32)]
+
+
+def build(force: bool = False) -> str:
+    src = os.path.join(_HERE, "oracle.c")
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-shared",
+                               "-fPIC", "-pthread", src, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        L.orc_render_pixels.argtypes = [P, P, P, ctypes.c_int64, P, P, P, P, P, ctypes.c_int]
+        L.orc_render_pixels.restype = ctypes.c_int
+        L.orc_f16_decode.argtypes = [ctypes.c_uint16]; L.orc_f16_decode.restype = ctypes.c_double
+        L.orc_f16_encode.argtypes = [ctypes.c_float]; L.orc_f16_encode.restype = ctypes.c_uint16
+        L.orc_e4m3_decode.argtypes = [ctypes.c_uint8]; L.orc_e4m3_decode.restype = ctypes.c_double
+        L.orc_e4m3_encode.argtypes = [ctypes.c_float]; L.orc_e4m3_encode.restype = ctypes.c_uint8
+        L.orc_fp8_scale.argtypes = [ctypes.c_int64, ctypes.c_int64, P, ctypes.c_int]
+        L.orc_fp8_scale.restype = ctypes.c_float
+        L.orc_quantize.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P, ctypes.c_int, ctypes.c_float, P]
+        L.orc_quantize.restype = None
+        for f in ("orc_bytes_nerf",):
+            getattr(L, f).argtypes = [ctypes.c_uint64] * 4
+            getattr(L, f).restype = ctypes.c_uint64
+        L.orc_bytes_fastnerf_pos.argtypes = [ctypes.c_uint64] * 4
+        L.orc_bytes_fastnerf_pos.restype = ctypes.c_uint64
+        L.orc_bytes_fastnerf_dir.argtypes = [ctypes.c_uint64] * 3
+        L.orc_bytes_fastnerf_dir.restype = ctypes.c_uint64
+        L.orc_ray.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P]
+        L.orc_ray.restype = None
+        L.orc_phi_key.argtypes = [ctypes.c_float, ctypes.c_float]; L.orc_phi_key.restype = ctypes.c_float
+        L.orc_dir_cell.argtypes = [ctypes.c_int, P, P, P]; L.orc_dir_cell.restype = None
+        L.orc_dt.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int32]; L.orc_dt.restype = ctypes.c_float
+        L.orc_s_thr.argtypes = [ctypes.c_float, ctypes.c_float]; L.orc_s_thr.restype = ctypes.c_int64
+        L.orc_fix.argtypes = [ctypes.c_double]; L.orc_fix.restype = ctypes.c_int64
+        L.orc_trace_fp64.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, P]
+        L.orc_trace_fp64.restype = None
+        L.orc_posenc.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P]
+        L.orc_posenc.restype = None
+        L.orc_mlp_forward.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_int64, P, P, ctypes.c_int]
+        L.orc_mlp_forward.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _nthreads(n):
+    return int(n) if n else max(1, os.cpu_count() or 1)
+
+
+# ------------------------------------------------------------------ structs
+class Cache:
+    """A cache as the oracle reads it: stored arrays (dense, unpadded) plus metadata.
+
+    sigma: [k^3] (float32 / uint16 FP16 bits / uint8 E4M3 codes), index (z*k + y)*k + x;
+    uvw: [k^3, 3D] same dtype, channels u_1..u_D, v_1..v_D, w_1..w_D;
+    beta: [l, l, D] float32 or uint16 FP16 bits, index [i_theta][i_phi];
+    scales: float32 [1 + 3D] for FP8 (sigma first).
+    field: optional (ctypes function pointer, user pointer) FP64 cell accessor
+    that replaces sigma/uvw.
+    """
+
+    def __init__(self, k, D, l, sigma, uvw, beta, pos_prec=FP32, dir_prec=FP32, scales=None,
+                 bmin=(-1.5, -1.5, -1.5), bmax=(1.5, 1.5, 1.5), field=None):
+        self.k, self.D, self.l = int(k), int(D), int(l)
+        self.pos_prec, self.dir_prec = pos_prec, dir_prec
+        self.sigma = None if sigma is None else np.ascontiguousarray(sigma).reshape(-1)
+        self.uvw = None if uvw is None else np.ascontiguousarray(uvw).reshape(-1)
+        self.beta = np.ascontiguousarray(beta).reshape(-1)
+        self.scales = None if scales is None else np.ascontiguousarray(scales, dtype=np.float32)
+        self.bmin, self.bmax = tuple(bmin), tuple(bmax)
+        self.field = field
+        s = _Cache()
+        s.k, s.D, s.l = self.k, self.D, self.l
+        s.bmin[:] = [float(v) for v in self.bmin]
+        s.bmax[:] = [float(v) for v in self.bmax]
+        s.pos_prec, s.dir_prec = pos_prec, dir_prec
+        s.sigma = None if self.sigma is None else self.sigma.ctypes.data
+        s.uvw = None if self.uvw is None else self.uvw.ctypes.data
+        s.beta = self.beta.ctypes.data
+        s.scales = None if self.scales is None else self.scales.ctypes.data
+        if field is not None:
+            fn, user = field
+            s.field = ctypes.cast(fn, ctypes.c_void_p).value
+            s.field_user = user
+        self._s = s
+
+
+def camera_struct(cam: dict) -> _Camera:
+    c = _Camera()
+    c.c2w[:] = [float(v) for v in np.asarray(cam["c2w"], dtype=np.float32).reshape(12)]
+    c.fx, c.fy, c.cx, c.cy = float(cam["fx"]), float(cam["fy"]), float(cam["cx"]), float(cam["cy"])
+    c.W, c.H = int(cam["W"]), int(cam["H"])
+    return c
+
+
+def params_struct(N, t_near=2.0, t_far=6.0, t_thr=1e-4, bg=(1.0, 1.0, 1.0), act=ACT_SIGMOID) -> _Params:
+    p = _Params()
+    p.N, p.t_near, p.t_far, p.t_thr = int(N), float(t_near), float(t_far), float(t_thr)
+    p.bg[:] = [float(v) for v in bg]
+    p.act = int(act)
+    return p
+
+
+# ------------------------------------------------------------------ rendering
+def render_pixels(cache: Cache, cam: dict, params: _Params, px, py, want_cells=False, nthreads=None):
+    """Render listed pixels. Returns (rgba [n,4] f64, stats [n,4] i32, cells [n,N] i32 or None)."""
+    px = np.ascontiguousarray(px, dtype=np.int32).reshape(-1)
+    py = np.ascontiguousarray(py, dtype=np.int32).reshape(-1)
+    n = px.size
+    rgba = np.zeros((n, 4))
+    stats = np.zeros((n, 4), dtype=np.int32)
+    cells = np.zeros((n, params.N), dtype=np.int32) if want_cells else None
+    cs = camera_struct(cam)
+    rc = lib().orc_render_pixels(ctypes.byref(cache._s), ctypes.byref(cs), ctypes.byref(params), n, _p(px), _p(py),
+                                 _p(rgba), _p(stats), _p(cells), _nthreads(nthreads))
+    if rc != 0:
+        raise ValueError("orc_render_pixels rejected its arguments")
+    return rgba, stats, cells
+
+
+def render_image(cache: Cache, cam: dict, params: _Params, want_cells=False, nthreads=None):
+    """Whole image: rgba [H,W,4], stats [H,W,4], cells [H,W,N] or None."""
+    W, H = int(cam["W"]), int(cam["H"])
+    py, px = np.meshgrid(np.arange(H, dtype=np.int32), np.arange(W, dtype=np.int32), indexing="ij")
+    rgba, stats, cells = render_pixels(cache, cam, params, px.reshape(-1), py.reshape(-1), want_cells, nthreads)
+    return (rgba.reshape(H, W, 4), stats.reshape(H, W, 4),
+            None if cells is None else cells.reshape(H, W, params.N))
+
+
+def ray(cam: dict, px: int, py: int):
+    d = np.zeros(3, dtype=np.float32)
+    o = np.zeros(3, dtype=np.float32)
+    cs = camera_struct(cam)
+    lib().orc_ray(ctypes.byref(cs), px, py, _p(d), _p(o))
+    return d, o
+
+
+def dir_cell(l: int, d) -> tuple:
+    d = np.ascontiguousarray(d, dtype=np.float32)
+    it = ctypes.c_int32()
+    ip = ctypes.c_int32()
+    lib().orc_dir_cell(l, _p(d), ctypes.byref(it), ctypes.byref(ip))
+    return it.value, ip.value
+
+
+def phi_key(x: float, y: float) -> float:
+    return lib().orc_phi_key(x, y)
+
+
+def dt(t_near, t_far, N) -> float:
+    return lib().orc_dt(t_near, t_far, N)
+
+
+def s_thr(t_thr, dt_) -> int:
+    return lib().orc_s_thr(t_thr, dt_)
+
+
+def fix(sigma: float) -> int:
+    return lib().orc_fix(sigma)
+
+
+def trace_fp64(cache: Cache, cam: dict, params: _Params, px: int, py: int):
+    N = params.N
+    cells = np.zeros(N, dtype=np.int32)
+    margin = np.zeros(N)
+    dc = ctypes.c_int32()
+    dm = ctypes.c_double()
+    cs = camera_struct(cam)
+    lib().orc_trace_fp64(ctypes.byref(cache._s), ctypes.byref(cs), ctypes.byref(params), px, py, _p(cells),
+                         _p(margin), ctypes.byref(dc), ctypes.byref(dm))
+    return cells, margin, dc.value, dm.value
+
+
+# ------------------------------------------------------------------ formats and quantisation
+def f16_encode(x) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float32).reshape(-1)
+    return np.array([lib().orc_f16_encode(float(v)) for v in x], dtype=np.uint16)
+
+
+def f16_decode(h) -> np.ndarray:
+    h = np.asarray(h, dtype=np.uint16).reshape(-1)
+    return np.array([lib().orc_f16_decode(int(v)) for v in h])
+
+
+def e4m3_encode(x) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float32).reshape(-1)
+    return np.array([lib().orc_e4m3_encode(float(v)) for v in x], dtype=np.uint8)
+
+
+def e4m3_decode(q) -> np.ndarray:
+    q = np.asarray(q, dtype=np.uint8).reshape(-1)
+    return np.array([lib().orc_e4m3_decode(int(v)) for v in q])
+
+
+def quantize_channel(prec: int, x: np.ndarray, clamp_nonneg: bool, scale: float = 1.0) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1)
+    dt_ = {FP32: np.float32, FP16: np.uint16, FP8: np.uint8}[prec]
+    out = np.zeros(x.size, dtype=dt_)
+    lib().orc_quantize(prec, x.size, 1, _p(x), int(clamp_nonneg), scale, _p(out))
+    return out
+
+
+def fp8_scale(x: np.ndarray, clamp_nonneg: bool) -> float:
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1)
+    return lib().orc_fp8_scale(x.size, 1, _p(x), int(clamp_nonneg))
+
+
+def quantize_cache(k, D, l, sigma, uvw, beta, pos_prec, dir_prec) -> Cache:
+    """The oracle's own quantisation of FP32 cache arrays into a stored-precision Cache."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.float32).reshape(-1)
+    uvw = np.ascontiguousarray(uvw, dtype=np.float32).reshape(-1, 3 * D)
+    beta = np.ascontiguousarray(beta, dtype=np.float32).reshape(-1)
+    scales = None
+    if pos_prec == FP8:
+        scales = np.zeros(1 + 3 * D, dtype=np.float32)
+        scales[0] = fp8_scale(sigma, True)
+        for c in range(3 * D):
+            scales[1 + c] = lib().orc_fp8_scale(uvw.shape[0], 3 * D, _p(uvw[:, c:]), 0)
+        qs = quantize_channel(FP8, sigma, True, scales[0])
+        qu = np.zeros(uvw.shape, dtype=np.uint8)
+        for c in range(3 * D):
+            col = np.ascontiguousarray(uvw[:, c])
+            qu[:, c] = quantize_channel(FP8, col, False, scales[1 + c])
+    elif pos_prec == FP16:
+        qs = quantize_channel(FP16, sigma, True)
+        qu = quantize_channel(FP16, uvw.reshape(-1), False).reshape(uvw.shape)
+    else:
+        qs = quantize_channel(FP32, sigma, True)
+        qu = uvw
+    qb = quantize_channel(FP16, beta, False) if dir_prec == FP16 else beta
+    return Cache(k, D, l, qs, qu, qb, pos_prec=pos_prec, dir_prec=dir_prec, scales=scales)
+
+
+# ------------------------------------------------------------------ cache sizes
+def bytes_nerf(k, l, s_sigma_bits=16, s_rgb_bits=24) -> int:
+    return int(lib().orc_bytes_nerf(k, l, s_sigma_bits, s_rgb_bits))
+
+
+def bytes_fastnerf(k, l, D, s_sigma_bits=16, s_uvw_bits=48, s_beta_bits=16) -> tuple:
+    """(position-cache bytes, direction-cache bytes) for a dense cache."""
+    return (int(lib().orc_bytes_fastnerf_pos(k, D, s_sigma_bits, s_uvw_bits)),
+            int(lib().orc_bytes_fastnerf_dir(l, D, s_beta_bits)))
+
+
+# ------------------------------------------------------------------ MLPs
+def posenc(x: np.ndarray, L: int, n_out: int) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n, n_in = x.shape
+    out = np.zeros((n, n_out))
+    lib().orc_posenc(n, n_in, L, _p(x), n_out, _p(out))
+    return out
+
+
+def mlp_forward(weights, biases, x: np.ndarray, round_bf16: bool, nthreads=None) -> np.ndarray:
+    """weights[i]: [out, in] FP64 (exact values of the stored bf16 weights); biases[i]: [out]."""
+    n_layers = len(weights)
+    dims = [weights[0].shape[1]] + [w.shape[0] for w in weights]
+    dims_a = np.array(dims, dtype=np.int32)
+    Ws = [np.ascontiguousarray(w, dtype=np.float64) for w in weights]
+    Bs = [np.ascontiguousarray(b, dtype=np.float64) for b in biases]
+    Wp = (ctypes.c_void_p * n_layers)(*[w.ctypes.data for w in Ws])
+    Bp = (ctypes.c_void_p * n_layers)(*[b.ctypes.data for b in Bs])
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros((x.shape[0], dims[-1]))
+    rc = lib().orc_mlp_forward(n_layers, _p(dims_a), Wp, Bp, int(round_bf16), x.shape[0], _p(x), _p(out),
+                               _nthreads(nthreads))
+    if rc != 0:
+        raise ValueError("orc_mlp_forward rejected its arguments")
+    return out

@@ -1,0 +1,381 @@
+"""Pins of the FP64 oracle against facts fixed by the paper or by mathematics.
+
+Each test checks the oracle against something other than itself: numbers the
+paper prints, closed forms of Eq. 1 on homogeneous media, reductions of Eq. 5,
+brute-force FP64 geometry with libm, and library number formats.
+"""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def axis_camera(W=64, H=64, f=80.0, eye=(0.0, 0.0, 4.0)):
+    """Camera at `eye` looking at the origin; cx, cy put pixel (W//2, H//2) on the optical axis."""
+    cam = scenegen.look_at_camera(eye, W, H)
+    cam["fx"] = np.float32(f)
+    cam["fy"] = np.float32(f)
+    cam["cx"] = np.float32(W // 2 + 0.5)
+    cam["cy"] = np.float32(H // 2 + 0.5)
+    return cam
+
+
+def const_cache(k, D, l, sigma0, uvw_vals, beta_vals, prec=oracle.FP32):
+    n = k ** 3
+    sig = np.full(n, sigma0, dtype=np.float32)
+    uvw = np.tile(np.asarray(uvw_vals, dtype=np.float32).reshape(1, 3 * D), (n, 1))
+    beta = np.tile(np.asarray(beta_vals, dtype=np.float32).reshape(1, D), (l * l, 1))
+    return oracle.Cache(k, D, l, sig, uvw, beta)
+
+
+# ------------------------------------------------------------------ cache sizes (printed integers)
+def test_cache_sizes_match_paper():
+    with open(os.path.join(GOLDEN, "cache_sizes.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        if c["formula"] == "nerf":
+            assert oracle.bytes_nerf(c["k"], c["l"], c["s_sigma_bits"], c["s_rgb_bits"]) == c["bytes"], c["cite"]
+        elif c["formula"] == "fastnerf":
+            pos, dirb = oracle.bytes_fastnerf(c["k"], c["l"], c["D"], c["s_sigma_bits"], c["s_uvw_bits"],
+                                              c["s_beta_bits"])
+            assert (pos, dirb) == (c["pos_bytes"], c["dir_bytes"]), c["cite"]
+        elif c["formula"] == "nerf_approx":
+            v = oracle.bytes_nerf(c["k"], c["l"], c["s_sigma_bits"], c["s_rgb_bits"])
+            assert abs(v / c["approx_bytes"] - 1) < c["rel_tol"], c["cite"]
+        elif c["formula"] == "fastnerf_approx":
+            pos, dirb = oracle.bytes_fastnerf(c["k"], c["l"], c["D"], c["s_sigma_bits"], c["s_uvw_bits"],
+                                              c["s_beta_bits"])
+            assert abs((pos + dirb) / c["approx_bytes"] - 1) < c["rel_tol"], c["cite"]
+
+
+# ------------------------------------------------------------------ Eq. 1: homogeneous medium closed forms
+@pytest.mark.parametrize("sigma0,expect_steps", [(2.0, 64), (0.5, 64), (50.0, 11), (7.0, None)])
+def test_homogeneous_box_closed_form(sigma0, expect_steps):
+    """All cells sigma0, colour c: C = c (1 - e^{-sigma0 m Delta}) + e^{-sigma0 m Delta} bg, m composited samples.
+
+    Central ray of a camera at (0,0,4) looking down -z: samples t_i = 2 + (i+1/2)/16 put
+    z = 2 - (i+1/2)/16, exact in binary32, inside [-1.5, 1.5) for i = 8..55 (48 samples).
+    m = min(48, m_thr) with m_thr the smallest m such that m sigma0 Delta >= ln(1/T_thr).
+    """
+    k, D, l, N = 64, 1, 8, 64
+    c = np.array([0.3, 0.5, 0.7], dtype=np.float32).astype(np.float64)  # stored binary32 values
+    cache = const_cache(k, D, l, sigma0, c, [1.0])
+    cam = axis_camera()
+    bg = (0.9, 0.2, 0.4)
+    p = oracle.params_struct(N, 2.0, 6.0, 1e-4, bg, oracle.ACT_IDENTITY)
+    rgba, st, cells = oracle.render_pixels(cache, cam, p, [32], [32], want_cells=True)
+    delta = 4.0 / N
+    m_thr = math.ceil(math.log(1e4) / (sigma0 * delta))
+    m = min(48, m_thr)
+    Tm = math.exp(-sigma0 * m * delta)
+    expect = c * (1 - Tm) + Tm * np.array(bg, dtype=np.float32).astype(np.float64)
+    np.testing.assert_allclose(rgba[0, :3], expect, rtol=0, atol=1e-12)
+    assert abs(rgba[0, 3] - (1 - Tm)) < 1e-12
+    n_steps = 8 + m if m_thr <= 48 else N
+    assert st[0, 0] == n_steps
+    if expect_steps is not None:
+        assert n_steps == expect_steps
+    assert st[0, 1] == m and st[0, 2] == m
+    # cells along the optical axis: x = y = 0 -> index 32; z from the exact sample depth
+    for i in range(N):
+        z = 2 - (i + 0.5) / 16
+        if i >= n_steps:
+            assert cells[0, i] == -2
+        elif i < 8 or i > 55:
+            assert cells[0, i] == -1
+        else:
+            iz = math.floor((z + 1.5) * 64 / 3)
+            assert cells[0, i] == (iz * k + 32) * k + 32
+
+
+def test_homogeneous_box_chord_form():
+    """Continuous Beer-Lambert along the chord: |C - (c (1-e^{-sL}) + e^{-sL} bg)| <= s * Delta (|n Delta - L| <= Delta)."""
+    k, N, sigma0 = 32, 256, 0.7
+    c = np.array([0.2, 0.6, 0.9], dtype=np.float32).astype(np.float64)
+    cache = const_cache(k, 1, 4, sigma0, c, [1.0])
+    cam = axis_camera()
+    bg = np.array([1.0, 1.0, 1.0])
+    p = oracle.params_struct(N, 2.0, 6.0, 0.0, tuple(bg), oracle.ACT_IDENTITY)
+    rgba, st, _ = oracle.render_pixels(cache, cam, p, [32], [32])
+    L = 3.0
+    TL = math.exp(-sigma0 * L)
+    expect = c * (1 - TL) + TL * bg
+    assert np.max(np.abs(rgba[0, :3] - expect)) <= sigma0 * (4.0 / N) + 1e-12
+    assert st[0, 0] == N  # T_thr = 0 disables termination
+
+
+def test_empty_cache_invariants(tiny_arrays):
+    sig, uvw, beta = tiny_arrays
+    w = scenegen.tiny()
+    cache = oracle.Cache(w.k, w.D, w.l, np.zeros_like(sig), uvw, beta)
+    bg = (0.25, 0.5, 1.0)
+    p = oracle.params_struct(w.n_samples, bg=bg)
+    rgba, st, _ = oracle.render_image(cache, w.cameras()[0], p)
+    assert np.all(rgba[..., :3] == np.array(bg))
+    assert np.all(rgba[..., 3] == 0.0)
+    assert np.all(st[..., 2] == 0) and np.all(st[..., 0] == w.n_samples)
+
+
+def test_transmittance_invariants_and_termination(tiny_arrays):
+    """0 <= 1-T <= 1; terminated rays stop at the first sample whose FP64 transmittance is <= T_thr."""
+    sig, uvw, beta = tiny_arrays
+    w = scenegen.tiny()
+    cache = oracle.Cache(w.k, w.D, w.l, sig, uvw, beta)
+    p = oracle.params_struct(w.n_samples)
+    cam = w.cameras()[0]
+    rgba, st, cells = oracle.render_image(cache, cam, p, want_cells=True)
+    A = rgba[..., 3]
+    assert np.all(A >= 0) and np.all(A <= 1)
+    assert np.all(rgba[..., :3] >= 0) and np.all(rgba[..., :3] <= 1 + 1e-12)  # sigmoid colours, white bg
+    flat_cells = cells.reshape(-1, w.n_samples)
+    sflat = sig.reshape(-1)
+    dt = 4.0 / w.n_samples
+    term = st[..., 0].reshape(-1) < w.n_samples
+    assert term.sum() > 100
+    for r in np.nonzero(term)[0][:400]:
+        n = st.reshape(-1, 4)[r, 0]
+        cs = flat_cells[r, :n]
+        od = np.cumsum([sflat[cc] * dt if cc >= 0 else 0.0 for cc in cs])
+        assert math.exp(-od[-1]) <= 1e-4 * (1 + 1e-9)
+        assert n == 1 or math.exp(-od[-2]) > 1e-4
+        assert abs((1 - A.reshape(-1)[r]) - math.exp(-od[-1])) < 1e-12
+        assert np.all(flat_cells[r, n:] == -2)
+
+
+# ------------------------------------------------------------------ Eq. 5 reductions
+def test_eq5_component_pairing():
+    """D=2, u=(1,0), v=(0,1), w=(0,0), beta=(b1,b2), identity: colour per sample = (b1, b2, 0)."""
+    k, l, N, sigma0 = 16, 8, 64, 3.0
+    b1, b2 = 0.375, -1.25
+    cache = const_cache(k, 2, l, sigma0, [1, 0, 0, 1, 0, 0], [b1, b2])
+    cam = axis_camera()
+    p = oracle.params_struct(N, bg=(0, 0, 0), act=oracle.ACT_IDENTITY)
+    rgba, _, _ = oracle.render_pixels(cache, cam, p, [32, 20, 40], [32, 31, 45])
+    A = rgba[:, 3]
+    np.testing.assert_allclose(rgba[:, 0], b1 * A, atol=1e-14)
+    np.testing.assert_allclose(rgba[:, 1], b2 * A, atol=1e-14)
+    np.testing.assert_allclose(rgba[:, 2], 0.0, atol=0)
+
+
+def test_eq5_dropped_component_reduction(tiny_arrays):
+    """D=2 with beta=(1, 0) renders exactly like D=1 with beta=1 on the first component."""
+    sig, uvw, _ = tiny_arrays
+    w = scenegen.tiny()
+    D = w.D
+    u1 = uvw[:, :, :, [0, D, 2 * D]].reshape(-1, 3)
+    rng = np.random.default_rng(5)
+    u2 = rng.standard_normal(u1.shape).astype(np.float32)
+    uvw2 = np.stack([u1[:, 0], u2[:, 0], u1[:, 1], u2[:, 1], u1[:, 2], u2[:, 2]], axis=1)
+    l = 16
+    c1 = oracle.Cache(w.k, 1, l, sig, u1, np.ones((l, l, 1), np.float32))
+    b2 = np.zeros((l, l, 2), np.float32)
+    b2[..., 0] = 1
+    c2 = oracle.Cache(w.k, 2, l, sig, uvw2, b2)
+    p = oracle.params_struct(w.n_samples)
+    cam = w.cameras()[0]
+    r1, s1, _ = oracle.render_image(c1, cam, p)
+    r2, s2, _ = oracle.render_image(c2, cam, p)
+    assert np.array_equal(r1, r2) and np.array_equal(s1[..., :3], s2[..., :3])
+
+
+def test_eq5_constant_beta_direction_permutation(tiny_arrays):
+    """With direction-independent beta, permuting the direction cache leaves the image unchanged."""
+    sig, uvw, beta = tiny_arrays
+    w = scenegen.tiny()
+    const_b = np.tile(beta[3, 5].reshape(1, 1, -1), (w.l, w.l, 1))
+    perm = np.random.default_rng(1).permutation(w.l * w.l)
+    shuffled = const_b.reshape(-1, w.D)[perm].reshape(w.l, w.l, w.D)
+    p = oracle.params_struct(w.n_samples)
+    cam = w.cameras()[0]
+    ra, _, _ = oracle.render_image(oracle.Cache(w.k, w.D, w.l, sig, uvw, const_b), cam, p)
+    rb, _, _ = oracle.render_image(oracle.Cache(w.k, w.D, w.l, sig, uvw, shuffled), cam, p)
+    assert np.array_equal(ra, rb)
+
+
+def test_sigmoid_activation_midpoint():
+    """u=v=w=0 under the sigmoid gives colour 1/2: closed form with c = 0.5."""
+    k, N, sigma0 = 16, 64, 2.0
+    cache = const_cache(k, 1, 4, sigma0, [0, 0, 0], [1.0])
+    p = oracle.params_struct(N, bg=(0, 0, 0), act=oracle.ACT_SIGMOID)
+    rgba, st, _ = oracle.render_pixels(cache, axis_camera(), p, [32], [32])
+    Tm = math.exp(-sigma0 * 48 * (4.0 / N))
+    np.testing.assert_allclose(rgba[0, :3], 0.5 * (1 - Tm), atol=1e-13)
+
+
+def test_identity_activation_linearity(tiny_arrays):
+    """Identity activation, bg = 0: the image is linear in beta (same density, same weights)."""
+    sig, uvw, beta = tiny_arrays
+    w = scenegen.tiny()
+    p = oracle.params_struct(w.n_samples, bg=(0, 0, 0), act=oracle.ACT_IDENTITY)
+    cam = w.cameras()[0]
+    b1 = (np.round(beta * 64) / 64).astype(np.float32)  # coarse values: 2 b1 - 3 b2 is exact in binary32
+    b2 = np.roll(b1, 7, axis=1)
+    r1, _, _ = oracle.render_image(oracle.Cache(w.k, w.D, w.l, sig, uvw, b1), cam, p)
+    r2, _, _ = oracle.render_image(oracle.Cache(w.k, w.D, w.l, sig, uvw, b2), cam, p)
+    r3, _, _ = oracle.render_image(oracle.Cache(w.k, w.D, w.l, sig, uvw, (2 * b1 - 3 * b2).astype(np.float32)),
+                                   cam, p)
+    np.testing.assert_allclose(r3[..., :3], 2 * r1[..., :3] - 3 * r2[..., :3], atol=1e-9)
+
+
+# ------------------------------------------------------------------ direction cell vs libm FP64
+def test_direction_cell_known_axes():
+    l = 64
+    assert oracle.dir_cell(l, [0, 0, 1]) == (0, 0)
+    assert oracle.dir_cell(l, [0, 0, -1]) == (l - 1, 0)
+    assert oracle.dir_cell(l, [1, 0, 0]) == (l // 2, 0)
+    assert oracle.dir_cell(l, [0, 1, 0]) == (l // 2, l // 4)
+    assert oracle.dir_cell(l, [-1, 0, 0]) == (l // 2, l // 2)
+    assert oracle.dir_cell(l, [0, -1, 0]) == (l // 2, 3 * l // 4)
+    s = math.sqrt(0.5)
+    assert oracle.dir_cell(l, [s, -1e-3, s])[1] == l - 1
+
+
+@pytest.mark.parametrize("l", [8, 64, 512, 768])
+def test_direction_cell_vs_fp64_libm(l):
+    rng = np.random.default_rng(l)
+    d = rng.standard_normal((3000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d = d.astype(np.float32)
+    dd = d.astype(np.float64)
+    th = np.arccos(np.clip(dd[:, 2], -1, 1))
+    ph = np.mod(np.arctan2(dd[:, 1], dd[:, 0]), 2 * np.pi)
+    ut, up = th * l / np.pi, ph * l / (2 * np.pi)
+    it_ref = np.minimum(np.floor(ut).astype(int), l - 1)
+    ip_ref = np.floor(up).astype(int) % l
+    near = (np.abs(ut - np.round(ut)) * np.pi / l < 1e-5) | (np.abs(up - np.round(up)) * 2 * np.pi / l < 1e-5)
+    bad = 0
+    for i in range(len(d)):
+        got = oracle.dir_cell(l, d[i])
+        if got != (it_ref[i], ip_ref[i]):
+            assert near[i], (i, got, it_ref[i], ip_ref[i])
+            bad += 1
+    assert bad <= 3
+
+
+def test_phi_key_monotone():
+    ang = np.sort(np.random.default_rng(3).uniform(0, 2 * np.pi, 20000))
+    keys = np.array([oracle.phi_key(np.float32(np.cos(a)), np.float32(np.sin(a))) for a in ang])
+    assert np.all(np.diff(keys) >= 0)
+    assert keys[0] >= 0 and keys[-1] <= 4
+
+
+# ------------------------------------------------------------------ position cells vs FP64 geometry
+def test_position_cells_vs_fp64_geometry(tiny_arrays):
+    """binary32 sample cells equal the all-FP64 ones except for samples within 1e-3 cells of a face."""
+    sig, uvw, beta = tiny_arrays
+    w = scenegen.tiny()
+    cache = oracle.Cache(w.k, w.D, w.l, np.zeros_like(sig), uvw, beta)  # no termination: every sample visited
+    p = oracle.params_struct(w.n_samples)
+    cam = w.cameras()[0]
+    rng = np.random.default_rng(0)
+    px = rng.integers(0, w.W, 300).astype(np.int32)
+    py = rng.integers(0, w.H, 300).astype(np.int32)
+    _, st, cells = oracle.render_pixels(cache, cam, p, px, py, want_cells=True)
+    mism = 0
+    total = 0
+    for i in range(len(px)):
+        c64, margin, dcell, dmargin = oracle.trace_fp64(cache, cam, p, int(px[i]), int(py[i]))
+        diff = c64 != cells[i]
+        assert np.all(margin[diff] < 1e-3)
+        mism += diff.sum()
+        total += len(c64)
+        if st[i, 3] != dcell:
+            assert dmargin < 1e-5
+    assert mism / total < 1e-3
+
+
+# ------------------------------------------------------------------ termination arithmetic
+def test_fixed_point_depth():
+    assert oracle.fix(50.0) == 50 * 2 ** 32
+    assert oracle.fix(0.0) == 0
+    f = float(np.float32(0.1))
+    assert oracle.fix(f) == math.floor(f * 2 ** 32)
+    assert oracle.fix(3e9) == 2 ** 63 - 1
+    assert oracle.dt(2.0, 6.0, 64) == 0.0625
+    assert oracle.s_thr(1e-4, 0.0625) == math.ceil(math.log(1 / float(np.float32(1e-4))) / 0.0625 * 2 ** 32)
+    assert oracle.s_thr(0.0, 0.0625) == 2 ** 63 - 1
+
+
+# ------------------------------------------------------------------ number formats vs libraries
+def test_fp16_codec_vs_numpy():
+    codes = np.arange(65536, dtype=np.uint16)
+    ref = codes.view(np.float16).astype(np.float64)
+    got = oracle.f16_decode(codes)
+    fin = np.isfinite(ref)
+    assert np.array_equal(got[fin], ref[fin]) and np.all(np.isnan(got[np.isnan(ref)]))
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(4000) * 10 ** rng.uniform(-9, 5, 4000),
+                        [65504, 65519.99, 65520, 1e9, -1e9, 2 ** -24, 2 ** -25, 3 * 2 ** -26, 0.0, -0.0,
+                         1 + 2 ** -11, 1 + 3 * 2 ** -11]]).astype(np.float32)
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float16).view(np.uint16)
+    assert np.array_equal(oracle.f16_encode(x), ref)
+
+
+def test_e4m3_codec_vs_torch():
+    torch = pytest.importorskip("torch")
+    codes = np.arange(256, dtype=np.uint8)
+    ref = torch.from_numpy(codes).view(torch.float8_e4m3fn).float().numpy().astype(np.float64)
+    got = oracle.e4m3_decode(codes)
+    fin = ~np.isnan(ref)
+    assert np.array_equal(got[fin], ref[fin]) and np.all(np.isnan(got[~fin]))
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.uniform(-448, 448, 3000), rng.standard_normal(3000) * 2.0 ** rng.uniform(-12, 8, 3000),
+                        [448, -448, 2 ** -9, 2 ** -10, 3 * 2 ** -10, 0.0, 1.0625, 1.1875, 15.5]]).astype(np.float32)
+    x = x[np.abs(x) <= 448]  # torch's cast is not saturating: compare in range only
+    ref_q = torch.from_numpy(x).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    assert np.array_equal(oracle.e4m3_encode(x), ref_q)
+    # saturating form: beyond the largest finite value (and infinities) -> +-448
+    assert list(oracle.e4m3_encode(np.array([500, -1e6, np.inf], np.float32))) == [0x7E, 0xFE, 0x7E]
+
+
+def test_quantised_cache_close_to_fp32(tiny_arrays):
+    """FP16 and FP8 caches render close to the FP32 one (property, any size)."""
+    sig, uvw, beta = tiny_arrays
+    w = scenegen.tiny()
+    p = oracle.params_struct(w.n_samples)
+    cam = w.cameras()[0]
+    ref, _, _ = oracle.render_image(oracle.Cache(w.k, w.D, w.l, sig, uvw, beta), cam, p)
+    for prec, min_psnr in ((oracle.FP16, 55.0), (oracle.FP8, 25.0)):
+        q = oracle.quantize_cache(w.k, w.D, w.l, sig, uvw, beta, prec, oracle.FP16)
+        img, _, _ = oracle.render_image(q, cam, p)
+        mse = np.mean((img[..., :3] - ref[..., :3]) ** 2)
+        assert 10 * math.log10(1 / mse) > min_psnr
+
+
+# ------------------------------------------------------------------ MLP pieces
+def test_posenc_closed_form():
+    x = np.array([[0.0, 0.5, -0.25]])
+    e = oracle.posenc(x, 3, 20)
+    want = []
+    for v in x[0]:
+        for j in range(3):
+            want += [math.sin(2 ** j * math.pi * v), math.cos(2 ** j * math.pi * v)]
+    np.testing.assert_allclose(e[0, :18], want, atol=1e-15)
+    assert np.all(e[0, 18:] == 0)
+    assert e[0, 0] == 0.0 and e[0, 1] == 1.0
+
+
+def test_mlp_forward_vs_numpy():
+    rng = np.random.default_rng(2)
+    dims = [12, 16, 16, 5]
+    Ws = [rng.standard_normal((dims[i + 1], dims[i])) for i in range(3)]
+    bs = [rng.standard_normal(dims[i + 1]) for i in range(3)]
+    x = rng.standard_normal((40, 12))
+    h = x
+    for i in range(3):
+        h = h @ Ws[i].T + bs[i]
+        if i < 2:
+            h = np.maximum(h, 0)
+    np.testing.assert_allclose(oracle.mlp_forward(Ws, bs, x, False), h, rtol=1e-12, atol=1e-12)
+    # bf16 rounding mode stays within bf16 error of the exact chain
+    hb = oracle.mlp_forward(Ws, bs, x, True)
+    assert np.max(np.abs(hb - h)) < 0.05 * np.max(np.abs(h))
