@@ -1,0 +1,238 @@
+/*
+ * fnr.h -- C ABI of libfnr, a GB300 (sm_103a) renderer for FastNeRF's cached
+ * representation (Garbin et al., "FastNeRF: High-Fidelity Neural Rendering at
+ * 200FPS", 2021).
+ *
+ * Problem statement (Sections 3.3 and 4): given a position cache (density
+ * sigma and a D-component deep radiance map (u, v, w) sampled on a k^3 grid
+ * over a bounding box) and a direction cache (D weights beta on an l x l grid
+ * of (theta, phi)), and a set of camera parameters, generate one ray per
+ * pixel, sample it, look both caches up by nearest neighbour, form the colour
+ * c = act(sum_i beta_i (u_i, v_i, w_i)) (Eq. 5) and alpha-composite the
+ * samples front to back (Eq. 1) until the transmittance is saturated
+ * (supplementary "Meshing & Rendering"), filling an RGBA buffer.
+ *
+ * Conventions
+ *  - Every call returns fnr_status; FNR_OK is 0. No C++ exception crosses the
+ *    ABI. fnr_last_error() returns a message for the calling thread's last
+ *    failed call; the library owns that string until the thread's next call.
+ *  - Pointers named *_dev are CUDA device pointers; they stay owned by the
+ *    caller, who must keep them alive until the work that uses them has
+ *    completed on its stream. Other pointers are host pointers, read during
+ *    the call only.
+ *  - fnr_stream_t is a cudaStream_t (NULL = legacy default stream).
+ *  - Work is stream-ordered: argument errors are returned at once; a CUDA
+ *    launch failure is returned as FNR_ERR_CUDA by the call that saw it.
+ *
+ * Geometry (exact definitions; the integer results -- cells, direction cell,
+ * termination step -- are bit-reproducible):
+ *  - Pixel (px, py), py = 0 the top row; camera looks down its -z axis.
+ *    binary32, correctly rounded, no contraction:
+ *      dcx = ((px + 0.5) - cx) / fx,  dcy = -(((py + 0.5) - cy) / fy)
+ *      w_r = fma(R_r0, dcx, fma(R_r1, dcy, -R_r2)), r = 0, 1, 2 (c2w rotation)
+ *      n2 = fma(wx, wx, fma(wy, wy, wz * wz)), d = w / sqrt(n2), o = c2w eye.
+ *  - Samples (Section 3.1, N midpoints on [t_near, t_far], delta_i = Delta):
+ *      Delta = (t_far - t_near) / N, t_i = fma(i + 0.5, Delta, t_near),
+ *      p = fma(t_i, d, o), g_a = (p_a - bmin_a) * s_a with
+ *      s_a = binary32(k / (bmax_a - bmin_a)) evaluated in FP64.
+ *    The sample is inside the cache iff 0 <= g_a < k on all axes; its cell is
+ *    floor(g) and its linear index (z * k + y) * k + x (Section 3.3, cell-
+ *    centred grid, nearest neighbour as in Section 4).
+ *  - Direction cell (Section 3.3, theta in [0, pi] from +z, phi = atan2(y, x)
+ *    in [0, 2 pi), l bins each):
+ *      i_theta = #{ j in 1..l-1 : d_z <= binary32(cos(j pi / l)) }
+ *      i_phi   = #{ j in 1..l-1 : key(d_x, d_y) >= binary32(key64(cos phi_j, sin phi_j)) },
+ *    phi_j = 2 pi j / l, key the monotone "diamond" azimuth key in [0, 4]:
+ *      y >= 0, x >= 0: y / (x + y);         y >= 0, x < 0: 1 + (-x) / (y + (-x));
+ *      y <  0, x <  0: 2 + (-y) / ((-x) + (-y)); y < 0, x >= 0: 3 + x / (x + (-y));
+ *      (0, 0) -> 0; key in binary32, key64 the same formula in FP64.
+ *  - Per occupied sample (sigma > 0): colour (Eq. 5) then Eq. 1 with
+ *    alpha = 1 - exp(-sigma Delta), T <- T exp(-sigma Delta). Termination:
+ *    S += floor(sigma * 2^32) (int64, saturating; 2^63-1 when sigma >= 2^31);
+ *    the ray stops after the first sample with S >= S_thr,
+ *    S_thr = ceil(ln(1 / t_thr) / Delta * 2^32) in FP64 (t_thr <= 0: never).
+ *    The background is added with the final transmittance:
+ *    RGB += T * bg, alpha = 1 - T.
+ */
+#ifndef FNR_H
+#define FNR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FNR_API __attribute__((visibility("default")))
+#else
+#define FNR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t fnr_status;
+#define FNR_OK 0
+#define FNR_ERR_INVALID_ARG 1 /* malformed argument; nothing was launched */
+#define FNR_ERR_UNSUPPORTED 2 /* valid but not supported by this build (e.g. D > 16) */
+#define FNR_ERR_OOM 3         /* a device allocation failed */
+#define FNR_ERR_BUDGET 4      /* the context's HBM budget would be exceeded */
+#define FNR_ERR_QUEUE_FULL 5  /* the request queue is full; retry later */
+#define FNR_ERR_NOT_READY 6   /* the request is still queued or in flight */
+#define FNR_ERR_TIMEOUT 7     /* a host wait ran out */
+#define FNR_ERR_CUDA 8        /* a CUDA runtime call failed */
+#define FNR_ERR_DEVICE 9      /* a kernel reported an error through its status word */
+
+#define FNR_PREC_FP32 0
+#define FNR_PREC_FP16 1
+#define FNR_PREC_FP8_E4M3 2 /* OCP E4M3 with one binary32 scale per channel */
+
+#define FNR_ACT_SIGMOID 0  /* c = 1 / (1 + exp(-x)) per channel */
+#define FNR_ACT_IDENTITY 1 /* c = x */
+
+#define FNR_SRC_ARRAYS 1
+#define FNR_SRC_MLP 2
+
+#define FNR_LOC_HOST 0
+#define FNR_LOC_DEVICE 1
+
+#define FNR_MAX_D 16
+#define FNR_MAX_K 2048
+#define FNR_MAX_L 4096
+#define FNR_MAX_SAMPLES 4096
+#define FNR_MAX_IMAGE_SIDE 16384
+
+typedef struct CUstream_st *fnr_stream_t;
+typedef struct fnr_context fnr_context;
+typedef struct fnr_cache fnr_cache;
+
+/* ------------------------------------------------------------------ context */
+/* Create a context on CUDA device `device`. hbm_budget_bytes caps the device
+ * memory the context allocates for caches plus the outputs of admitted
+ * serving requests (0 = no cap). Errors: INVALID_ARG (bad device), CUDA. */
+FNR_API fnr_status fnr_context_create(int32_t device, uint64_t hbm_budget_bytes, fnr_context **out);
+/* Stops the request loop (outstanding requests finish first), frees every
+ * cache the context still owns and the context. NULL is a no-op. */
+FNR_API fnr_status fnr_context_destroy(fnr_context *ctx);
+/* Bytes currently charged against the budget. */
+FNR_API uint64_t fnr_context_used_bytes(const fnr_context *ctx);
+
+/* Thread-local message of the last failed call ("" if none). */
+FNR_API const char *fnr_last_error(void);
+
+/* ------------------------------------------------------------------ caches */
+typedef struct {
+    int32_t k;             /* grid samples per axis of the position cache, 1..FNR_MAX_K */
+    int32_t D;             /* components of the deep radiance map, 1..FNR_MAX_D */
+    int32_t l;             /* direction bins per angle, 2..FNR_MAX_L */
+    int32_t pos_precision; /* storage of sigma and (u, v, w): FNR_PREC_* */
+    int32_t dir_precision; /* storage of beta: FNR_PREC_FP32 or FNR_PREC_FP16 */
+    int32_t reserved0;
+    float bmin[3], bmax[3]; /* bounding box V, bmax > bmin on every axis */
+} fnr_cache_desc;
+
+/* One MLP for the tensor-core cache build (Section 3.2, Eqs. 3 and 4; Section 4):
+ * input = positional encoding gamma(x) = [sin(2^j pi x_a), cos(2^j pi x_a)],
+ * a = 0..pe_in-1 (coordinate-major), j = 0..pe_freqs-1 (sin before cos),
+ * zero padded to dims[0]; hidden layers ReLU; last layer linear.
+ * weights[i]: device bf16 bits, [dims[i+1]][dims[i]] row-major;
+ * biases[i]: device float[dims[i+1]]. */
+typedef struct {
+    int32_t n_layers;  /* 1..16 */
+    int32_t pe_in;     /* raw inputs: 3 (position) */
+    int32_t pe_freqs;  /* L */
+    int32_t dims[17];  /* dims[0] = padded encoded width, dims[n_layers] = outputs */
+    const uint16_t *weights[16];
+    const float *biases[16];
+} fnr_mlp;
+
+typedef struct {
+    int32_t kind;     /* FNR_SRC_ARRAYS or FNR_SRC_MLP */
+    int32_t location; /* FNR_SRC_ARRAYS: FNR_LOC_HOST or FNR_LOC_DEVICE */
+    /* FNR_SRC_ARRAYS, binary32:
+     *   sigma [k^3] at (z*k + y)*k + x; negative and NaN densities are stored as 0
+     *   uvw   [k^3][3D], channels u_1..u_D, v_1..v_D, w_1..w_D
+     *   beta  [l][l][D] at (i_theta*l + i_phi)*D + i, sampled at bin centres
+     * FP16: round to nearest even. FP8: scale_c = absmax_c / 448 in binary32
+     * (1 if the channel is all zero), q = E4M3(x / scale_c), round to nearest
+     * even, saturating to +-448. */
+    const float *sigma;
+    const float *uvw;
+    const float *beta;
+    /* FNR_SRC_MLP (device bf16 MLPs, built on the tensor cores):
+     * F_pos: 3 -> dims_out = 1 + 3D; sigma = ReLU(out[0]), (u, v, w) = out[1..3D]
+     * evaluated at the cell centres bmin + (j + 1/2)(bmax - bmin)/k.
+     * F_dir: unit direction (3 inputs) -> D outputs = beta, evaluated at the bin
+     * centres theta = (i + 1/2) pi / l, phi = (j + 1/2) 2 pi / l. */
+    const fnr_mlp *pos_mlp;
+    const fnr_mlp *dir_mlp;
+} fnr_cache_source;
+
+/* Bytes of the dense caches by the supplementary "Cache size calculation"
+ * (second version, alpha = 1): k^3 (s_sigma + D s_uvw) + D s_beta l^2, where
+ * s_uvw is one (u_i, v_i, w_i) triple; FP8 adds its (1 + 3D) binary32 scales.
+ * Returns 0 for an invalid descriptor. */
+FNR_API uint64_t fnr_cache_bytes(const fnr_cache_desc *desc);
+/* Device bytes one cache occupies: the above plus record padding to 16 bytes
+ * (8 for FP8), 256-byte section alignment and the two direction-bin tables. */
+FNR_API uint64_t fnr_cache_footprint(const fnr_cache_desc *desc);
+
+/* Build a cache on `stream`. Returns when the cache is complete (the call
+ * synchronises `stream`). The library owns the cache until fnr_cache_free.
+ * Errors: INVALID_ARG, UNSUPPORTED, BUDGET, OOM, CUDA. */
+FNR_API fnr_status fnr_build_cache(fnr_context *ctx, const fnr_cache_desc *desc, const fnr_cache_source *src,
+                           fnr_stream_t stream, fnr_cache **out);
+/* Free a cache. INVALID_ARG if serving requests still reference it. */
+FNR_API fnr_status fnr_cache_free(fnr_context *ctx, fnr_cache *cache);
+
+/* Device layout of a built cache (read-only views, owned by the cache). */
+typedef struct {
+    const void *sigma_dev;     /* [k^3] stored density (float / half / e4m3) */
+    const void *uvw_dev;       /* [k^3] records of 3D stored values, record_stride bytes apart */
+    const void *beta_dev;      /* [l][l][D] stored weights */
+    const float *scales_dev;   /* FP8: [1 + 3D] (sigma first), else NULL */
+    const float *cos_theta_dev;/* [l] binary32(cos(j pi / l)); entry 0 = 1 */
+    const float *phi_key_dev;  /* [l] azimuth-key boundaries; entry 0 = 0 */
+    int32_t record_stride;     /* bytes between (u, v, w) records */
+    int32_t reserved0;
+    uint64_t footprint;        /* device bytes */
+} fnr_cache_layout;
+FNR_API fnr_status fnr_cache_get_layout(const fnr_cache *cache, fnr_cache_layout *out);
+
+/* ------------------------------------------------------------------ rendering */
+typedef struct {
+    float c2w[12]; /* row-major 3x4 [R | eye], camera-to-world */
+    float fx, fy, cx, cy;
+    int32_t width, height; /* 1..FNR_MAX_IMAGE_SIDE */
+} fnr_camera;
+
+typedef struct {
+    int32_t n_samples;     /* N, 1..FNR_MAX_SAMPLES */
+    float t_near, t_far;   /* finite, t_far > t_near */
+    float t_thr;           /* termination transmittance; <= 0 disables */
+    float bg[3];           /* background colour */
+    int32_t activation;    /* FNR_ACT_* */
+} fnr_render_params;
+
+typedef struct {
+    int32_t n_steps;    /* samples visited (i + 1 of the terminating sample, else N) */
+    int32_t n_lookups;  /* visited samples inside the cache box */
+    int32_t n_occupied; /* visited samples with sigma > 0 */
+    int32_t dir_cell;   /* i_theta * l + i_phi */
+} fnr_ray_stats;
+
+/* Render n_cams views of one cache (the plain path: one launch per call; up
+ * to 32 views share a launch). Frame f's pixels start at pixel offset
+ * P_f = sum_{g<f} W_g H_g:
+ *   rgba_dev        float[P][4], (R, G, B, alpha) at P_f + py * W_f + px
+ *   stats_dev       fnr_ray_stats[P] or NULL
+ *   debug_cells_dev int32[P][n_samples] or NULL: per sample its cell index,
+ *                   -1 outside the box, -2 after termination (needs k^3 < 2^31).
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+FNR_API fnr_status fnr_render(fnr_context *ctx, const fnr_cache *cache, const fnr_camera *cams, int32_t n_cams,
+                      const fnr_render_params *params, float *rgba_dev, fnr_ray_stats *stats_dev,
+                      int32_t *debug_cells_dev, fnr_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FNR_H */

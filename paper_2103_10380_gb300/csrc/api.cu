@@ -1,0 +1,471 @@
+// api.cu -- libfnr's C ABI: contexts, cache build/free, plain rendering.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "fnr_internal.h"
+
+namespace fnr {
+
+static thread_local std::string g_last_error;
+
+fnr_status fail(fnr_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+fnr_status cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) return fail(FNR_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(FNR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void clear_error() { g_last_error.clear(); }
+
+size_t elem_bytes(int prec) { return prec == FNR_PREC_FP32 ? 4 : prec == FNR_PREC_FP16 ? 2 : 1; }
+
+int rec_stride_bytes(int prec, int D) {
+    const int raw = 3 * D * static_cast<int>(elem_bytes(prec));
+    const int align = prec == FNR_PREC_FP8_E4M3 ? 8 : 16;
+    return (raw + align - 1) / align * align;
+}
+
+static uint64_t align256(uint64_t v) { return (v + 255u) & ~uint64_t(255u); }
+
+struct Layout {
+    uint64_t off_sigma, off_uvw, off_beta, off_ct, off_qp, off_scales, total;
+    int rec_stride;
+};
+
+static bool desc_valid(const fnr_cache_desc *d) {
+    if (!d) return false;
+    if (d->k < 1 || d->k > FNR_MAX_K || d->D < 1 || d->D > FNR_MAX_D || d->l < 2 || d->l > FNR_MAX_L) return false;
+    if (d->pos_precision < FNR_PREC_FP32 || d->pos_precision > FNR_PREC_FP8_E4M3) return false;
+    if (d->dir_precision != FNR_PREC_FP32 && d->dir_precision != FNR_PREC_FP16) return false;
+    for (int a = 0; a < 3; ++a)
+        if (!(isfinite(d->bmin[a]) && isfinite(d->bmax[a]) && d->bmax[a] > d->bmin[a])) return false;
+    return true;
+}
+
+static Layout layout_of(const fnr_cache_desc *d) {
+    Layout L;
+    const uint64_t k3 = uint64_t(d->k) * d->k * d->k;
+    L.rec_stride = rec_stride_bytes(d->pos_precision, d->D);
+    uint64_t off = 0;
+    L.off_sigma = off;
+    off = align256(off + k3 * elem_bytes(d->pos_precision));
+    L.off_uvw = off;
+    off = align256(off + k3 * uint64_t(L.rec_stride));
+    L.off_beta = off;
+    off = align256(off + uint64_t(d->l) * d->l * d->D * elem_bytes(d->dir_precision));
+    L.off_ct = off;
+    off = align256(off + uint64_t(d->l) * 4);
+    L.off_qp = off;
+    off = align256(off + uint64_t(d->l) * 4);
+    L.off_scales = off;
+    off = align256(off + uint64_t(1 + 3 * d->D) * 4);
+    L.total = off;
+    return L;
+}
+
+// Direction-bin boundary tables (see fnr.h): cos(j pi / l) and the azimuth key
+// of the unit vector at phi_j = 2 pi j / l, both in FP64 rounded to binary32.
+static double azimuth_key64(double x, double y) {
+    if (x == 0.0 && y == 0.0) return 0.0;
+    if (y >= 0.0) {
+        if (x >= 0.0) return y / (x + y);
+        return 1.0 + (-x) / (y - x);
+    }
+    if (x < 0.0) return 2.0 + (-y) / (-x - y);
+    return 3.0 + x / (x - y);
+}
+
+static void bin_tables(int l, std::vector<float> &ct, std::vector<float> &qp) {
+    const double pi = 3.14159265358979323846264338327950288;
+    ct.assign(l, 1.0f);
+    qp.assign(l, 0.0f);
+    for (int j = 1; j < l; ++j) {
+        ct[j] = static_cast<float>(cos(static_cast<double>(j) * pi / static_cast<double>(l)));
+        const double ph = 2.0 * pi * static_cast<double>(j) / static_cast<double>(l);
+        qp[j] = static_cast<float>(azimuth_key64(cos(ph), sin(ph)));
+    }
+}
+
+static bool charge(fnr_context *ctx, uint64_t bytes) {
+    uint64_t cur = ctx->used.load();
+    for (;;) {
+        if (ctx->budget && cur + bytes > ctx->budget) return false;
+        if (ctx->used.compare_exchange_weak(cur, cur + bytes)) return true;
+    }
+}
+
+static void uncharge(fnr_context *ctx, uint64_t bytes) { ctx->used.fetch_sub(bytes); }
+
+// RAII device buffer for build-time temporaries.
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+static fnr_status build_from_arrays(fnr_cache *c, const fnr_cache_source *src, const Layout &L, cudaStream_t s) {
+    const fnr_cache_desc &d = c->desc;
+    const int64_t k3 = int64_t(d.k) * d.k * d.k;
+    const int nch = 3 * d.D;
+    const int prec = d.pos_precision;
+    char *base = static_cast<char *>(c->base);
+    float *scales = reinterpret_cast<float *>(base + L.off_scales);
+    cudaError_t e;
+    const bool dev = src->location == FNR_LOC_DEVICE;
+    // Slab size for staging host arrays (cells per slab).
+    const int64_t slab = dev ? k3 : std::max<int64_t>(1, std::min<int64_t>(k3, (int64_t(256) << 20) / (4 * (nch + 1))));
+    DevBuf stage;
+    if (!dev) {
+        if ((e = cudaMalloc(&stage.p, size_t(slab) * 4 * (nch + 1))) != cudaSuccess) return cuda_fail(e, "staging");
+    }
+    auto slab_ptrs = [&](int64_t c0, int64_t n, const float **sp, const float **up) -> cudaError_t {
+        if (dev) {
+            *sp = src->sigma + c0;
+            *up = src->uvw + c0 * nch;
+            return cudaSuccess;
+        }
+        float *ss = static_cast<float *>(stage.p);
+        float *uu = ss + slab;
+        cudaError_t ee = cudaMemcpyAsync(ss, src->sigma + c0, size_t(n) * 4, cudaMemcpyHostToDevice, s);
+        if (ee == cudaSuccess)
+            ee = cudaMemcpyAsync(uu, src->uvw + c0 * nch, size_t(n) * 4 * nch, cudaMemcpyHostToDevice, s);
+        *sp = ss;
+        *up = uu;
+        return ee;
+    };
+    if (prec == FNR_PREC_FP8_E4M3) {
+        DevBuf amax;
+        if ((e = cudaMalloc(&amax.p, sizeof(unsigned) * (1 + nch))) != cudaSuccess) return cuda_fail(e, "absmax");
+        if ((e = cudaMemsetAsync(amax.p, 0, sizeof(unsigned) * (1 + nch), s)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+        for (int64_t c0 = 0; c0 < k3; c0 += slab) {
+            const int64_t n = std::min(slab, k3 - c0);
+            const float *sp, *up;
+            if ((e = slab_ptrs(c0, n, &sp, &up)) != cudaSuccess) return cuda_fail(e, "upload");
+            if ((e = launch_absmax(sp, up, n, nch, static_cast<unsigned *>(amax.p), s)) != cudaSuccess)
+                return cuda_fail(e, "absmax kernel");
+            if (!dev && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "absmax sync");
+        }
+        if ((e = launch_scales_from_absmax(static_cast<unsigned *>(amax.p), scales, 1 + nch, s)) != cudaSuccess)
+            return cuda_fail(e, "scales kernel");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "scales sync");
+    }
+    for (int64_t c0 = 0; c0 < k3; c0 += slab) {
+        const int64_t n = std::min(slab, k3 - c0);
+        const float *sp, *up;
+        if ((e = slab_ptrs(c0, n, &sp, &up)) != cudaSuccess) return cuda_fail(e, "upload");
+        if ((e = launch_convert_sigma(sp, base + L.off_sigma + c0 * elem_bytes(prec), n, prec, scales, s)) !=
+            cudaSuccess)
+            return cuda_fail(e, "density conversion");
+        if ((e = launch_convert_uvw(up, base + L.off_uvw + c0 * L.rec_stride, n, d.D, prec, L.rec_stride, scales,
+                                    s)) != cudaSuccess)
+            return cuda_fail(e, "uvw conversion");
+        if (!dev && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "conversion sync");
+    }
+    // direction cache
+    const int64_t nb = int64_t(d.l) * d.l * d.D;
+    const float *bp = src->beta;
+    DevBuf bstage;
+    if (!dev) {
+        if ((e = cudaMalloc(&bstage.p, size_t(nb) * 4)) != cudaSuccess) return cuda_fail(e, "beta staging");
+        if ((e = cudaMemcpyAsync(bstage.p, src->beta, size_t(nb) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "beta upload");
+        bp = static_cast<const float *>(bstage.p);
+    }
+    if ((e = launch_convert_beta(bp, base + L.off_beta, nb, d.dir_precision, s)) != cudaSuccess)
+        return cuda_fail(e, "beta conversion");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "build sync");
+    return FNR_OK;
+}
+
+static void fill_view(fnr_cache *c, const Layout &L) {
+    const fnr_cache_desc &d = c->desc;
+    char *base = static_cast<char *>(c->base);
+    CacheView &v = c->view;
+    v.sigma = base + L.off_sigma;
+    v.uvw = base + L.off_uvw;
+    v.beta = base + L.off_beta;
+    v.ct = reinterpret_cast<const float *>(base + L.off_ct);
+    v.qp = reinterpret_cast<const float *>(base + L.off_qp);
+    v.scales = reinterpret_cast<const float *>(base + L.off_scales);
+    for (int a = 0; a < 3; ++a) {
+        v.bmin[a] = d.bmin[a];
+        v.scale[a] = static_cast<float>(static_cast<double>(d.k) /
+                                        (static_cast<double>(d.bmax[a]) - static_cast<double>(d.bmin[a])));
+    }
+    v.kf = static_cast<float>(d.k);
+    v.k = d.k;
+    v.D = d.D;
+    v.l = d.l;
+    v.rec_stride = L.rec_stride;
+    v.pos_prec = d.pos_precision;
+    v.dir_prec = d.dir_precision;
+}
+
+// Fill the render constants shared by the plain and served paths.
+fnr_status make_render_const(const fnr_render_params *p, RenderConst *rc) {
+    if (!p) return fail(FNR_ERR_INVALID_ARG, "params is NULL");
+    if (p->n_samples < 1 || p->n_samples > FNR_MAX_SAMPLES)
+        return fail(FNR_ERR_INVALID_ARG, "n_samples %d outside [1, %d]", p->n_samples, FNR_MAX_SAMPLES);
+    if (!(isfinite(p->t_near) && isfinite(p->t_far) && p->t_far > p->t_near))
+        return fail(FNR_ERR_INVALID_ARG, "need finite t_near < t_far");
+    if (isnan(p->t_thr)) return fail(FNR_ERR_INVALID_ARG, "t_thr is NaN");
+    if (p->activation != FNR_ACT_SIGMOID && p->activation != FNR_ACT_IDENTITY)
+        return fail(FNR_ERR_INVALID_ARG, "unknown activation %d", p->activation);
+    rc->N = p->n_samples;
+    rc->t_near = p->t_near;
+    rc->dt = (p->t_far - p->t_near) / static_cast<float>(p->n_samples);
+    if (!(rc->dt > 0.0f)) return fail(FNR_ERR_INVALID_ARG, "sample spacing underflows");
+    rc->act = p->activation;
+    if (!(p->t_thr > 0.0f)) {
+        rc->s_thr = 0x7fffffffffffffffLL;
+    } else {
+        const double v = ceil(log(1.0 / static_cast<double>(p->t_thr)) / static_cast<double>(rc->dt) * 4294967296.0);
+        rc->s_thr = v >= 9223372036854775807.0 ? 0x7fffffffffffffffLL : (v < 0.0 ? 0 : static_cast<long long>(v));
+    }
+    for (int c = 0; c < 3; ++c) rc->bg[c] = p->bg[c];
+    rc->pad = 0;
+    return FNR_OK;
+}
+
+fnr_status check_camera(const fnr_camera *c) {
+    if (c->width < 1 || c->height < 1 || c->width > FNR_MAX_IMAGE_SIDE || c->height > FNR_MAX_IMAGE_SIDE)
+        return fail(FNR_ERR_INVALID_ARG, "image size %dx%d outside [1, %d]", c->width, c->height, FNR_MAX_IMAGE_SIDE);
+    for (int i = 0; i < 12; ++i)
+        if (!isfinite(c->c2w[i])) return fail(FNR_ERR_INVALID_ARG, "non-finite c2w");
+    if (!(isfinite(c->fx) && isfinite(c->fy) && c->fx != 0.0f && c->fy != 0.0f && isfinite(c->cx) && isfinite(c->cy)))
+        return fail(FNR_ERR_INVALID_ARG, "bad intrinsics");
+    return FNR_OK;
+}
+
+void fill_frame(FrameDesc *f, const fnr_camera *cam, float *rgba, fnr_ray_stats *stats, int32_t *cells,
+                int tile_begin) {
+    memcpy(f->c2w, cam->c2w, sizeof(f->c2w));
+    f->fx = cam->fx;
+    f->fy = cam->fy;
+    f->cx = cam->cx;
+    f->cy = cam->cy;
+    f->W = cam->width;
+    f->H = cam->height;
+    f->tiles_x = (cam->width + kTileW - 1) / kTileW;
+    f->tile_begin = tile_begin;
+    f->rgba = rgba;
+    f->stats = stats;
+    f->cells = cells;
+}
+
+int frame_tiles(const fnr_camera *cam) {
+    return ((cam->width + kTileW - 1) / kTileW) * ((cam->height + kTileH - 1) / kTileH);
+}
+
+bool cache_belongs(fnr_context *ctx, const fnr_cache *c) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    return ctx->caches.count(const_cast<fnr_cache *>(c)) != 0;
+}
+
+}  // namespace fnr
+
+using namespace fnr;
+
+extern "C" {
+
+const char *fnr_last_error(void) { return g_last_error.c_str(); }
+
+fnr_status fnr_context_create(int32_t device, uint64_t hbm_budget_bytes, fnr_context **out) {
+    clear_error();
+    if (!out) return fail(FNR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(FNR_ERR_INVALID_ARG, "device %d not in [0, %d)", device, n);
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    fnr_context *ctx = new fnr_context();
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    *out = ctx;
+    return FNR_OK;
+}
+
+fnr_status fnr_context_destroy(fnr_context *ctx) {
+    clear_error();
+    if (!ctx) return FNR_OK;
+    cudaSetDevice(ctx->device);
+    std::set<fnr_cache *> cs;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        cs.swap(ctx->caches);
+    }
+    for (fnr_cache *c : cs) {
+        if (c->owned && c->base) cudaFree(c->base);
+        delete c;
+    }
+    delete ctx;
+    return FNR_OK;
+}
+
+uint64_t fnr_context_used_bytes(const fnr_context *ctx) { return ctx ? ctx->used.load() : 0; }
+
+uint64_t fnr_cache_bytes(const fnr_cache_desc *d) {
+    if (!desc_valid(d)) return 0;
+    const uint64_t k3 = uint64_t(d->k) * d->k * d->k;
+    const uint64_t s_sigma = elem_bytes(d->pos_precision) * 8u;
+    const uint64_t s_uvw = 3u * elem_bytes(d->pos_precision) * 8u;
+    const uint64_t s_beta = elem_bytes(d->dir_precision) * 8u;
+    uint64_t bits = (uint64_t(d->D) * s_uvw + s_sigma) * k3 + uint64_t(d->D) * s_beta * d->l * d->l;
+    uint64_t bytes = bits / 8u;
+    if (d->pos_precision == FNR_PREC_FP8_E4M3) bytes += uint64_t(1 + 3 * d->D) * 4u;
+    return bytes;
+}
+
+uint64_t fnr_cache_footprint(const fnr_cache_desc *d) {
+    if (!desc_valid(d)) return 0;
+    return layout_of(d).total;
+}
+
+fnr_status fnr_build_cache(fnr_context *ctx, const fnr_cache_desc *desc, const fnr_cache_source *src,
+                           fnr_stream_t stream, fnr_cache **out) {
+    clear_error();
+    if (!ctx || !desc || !src || !out) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (!desc_valid(desc)) return fail(FNR_ERR_INVALID_ARG, "invalid cache descriptor");
+    if (src->kind == FNR_SRC_MLP) return fail(FNR_ERR_UNSUPPORTED, "MLP source not available in this build");
+    if (src->kind != FNR_SRC_ARRAYS) return fail(FNR_ERR_INVALID_ARG, "unknown source kind %d", src->kind);
+    if (!src->sigma || !src->uvw || !src->beta) return fail(FNR_ERR_INVALID_ARG, "NULL source array");
+    if (src->location != FNR_LOC_HOST && src->location != FNR_LOC_DEVICE)
+        return fail(FNR_ERR_INVALID_ARG, "unknown source location");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    const Layout L = layout_of(desc);
+    if (!charge(ctx, L.total))
+        return fail(FNR_ERR_BUDGET, "cache needs %llu bytes, budget %llu, in use %llu", (unsigned long long)L.total,
+                    (unsigned long long)ctx->budget, (unsigned long long)ctx->used.load());
+    fnr_cache *c = new fnr_cache();
+    c->desc = *desc;
+    c->footprint = L.total;
+    c->ctx = ctx;
+    if ((e = cudaMalloc(&c->base, L.total)) != cudaSuccess) {
+        uncharge(ctx, L.total);
+        delete c;
+        return cuda_fail(e, "cache allocation");
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<float> ct, qp;
+    bin_tables(desc->l, ct, qp);
+    char *base = static_cast<char *>(c->base);
+    fnr_status st = FNR_OK;
+    if ((e = cudaMemcpyAsync(base + L.off_ct, ct.data(), ct.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(base + L.off_qp, qp.data(), qp.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+        st = cuda_fail(e, "table upload");
+    }
+    if (st == FNR_OK && desc->pos_precision != FNR_PREC_FP8_E4M3) {
+        // scales unused: keep them defined (1.0)
+        std::vector<float> ones(1 + 3 * desc->D, 1.0f);
+        if ((e = cudaMemcpyAsync(base + L.off_scales, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            st = cuda_fail(e, "scale upload");
+        if (st == FNR_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "sync");
+    }
+    if (st == FNR_OK) st = build_from_arrays(c, src, L, s);
+    if (st != FNR_OK) {
+        cudaFree(c->base);
+        uncharge(ctx, L.total);
+        delete c;
+        return st;
+    }
+    fill_view(c, L);
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->caches.insert(c);
+    }
+    *out = c;
+    return FNR_OK;
+}
+
+fnr_status fnr_cache_free(fnr_context *ctx, fnr_cache *c) {
+    clear_error();
+    if (!ctx || !c) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (!ctx->caches.count(c)) return fail(FNR_ERR_INVALID_ARG, "cache does not belong to this context");
+        if (c->inflight.load() != 0) return fail(FNR_ERR_INVALID_ARG, "cache is referenced by in-flight requests");
+        ctx->caches.erase(c);
+    }
+    cudaSetDevice(ctx->device);
+    if (c->owned && c->base) cudaFree(c->base);
+    uncharge(ctx, c->footprint);
+    delete c;
+    return FNR_OK;
+}
+
+fnr_status fnr_cache_get_layout(const fnr_cache *c, fnr_cache_layout *out) {
+    clear_error();
+    if (!c || !out) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
+    const CacheView &v = c->view;
+    out->sigma_dev = v.sigma;
+    out->uvw_dev = v.uvw;
+    out->beta_dev = v.beta;
+    out->scales_dev = c->desc.pos_precision == FNR_PREC_FP8_E4M3 ? v.scales : nullptr;
+    out->cos_theta_dev = v.ct;
+    out->phi_key_dev = v.qp;
+    out->record_stride = v.rec_stride;
+    out->reserved0 = 0;
+    out->footprint = c->footprint;
+    return FNR_OK;
+}
+
+fnr_status fnr_render(fnr_context *ctx, const fnr_cache *cache, const fnr_camera *cams, int32_t n_cams,
+                      const fnr_render_params *params, float *rgba_dev, fnr_ray_stats *stats_dev,
+                      int32_t *debug_cells_dev, fnr_stream_t stream) {
+    clear_error();
+    if (!ctx || !cache || !cams || !rgba_dev) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
+    if (n_cams < 1) return fail(FNR_ERR_INVALID_ARG, "n_cams must be >= 1");
+    if (!cache_belongs(ctx, cache)) return fail(FNR_ERR_INVALID_ARG, "cache does not belong to this context");
+    RenderConst rc;
+    fnr_status st = make_render_const(params, &rc);
+    if (st != FNR_OK) return st;
+    for (int i = 0; i < n_cams; ++i)
+        if ((st = check_camera(&cams[i])) != FNR_OK) return st;
+    if (debug_cells_dev && uint64_t(cache->desc.k) * cache->desc.k * cache->desc.k >= (uint64_t(1) << 31))
+        return fail(FNR_ERR_UNSUPPORTED, "debug cells need k^3 < 2^31");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    MarchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.c = cache->view;
+    a.r = rc;
+    int64_t pix_off = 0;
+    for (int f0 = 0; f0 < n_cams; f0 += kMaxFramesPerLaunch) {
+        const int nf = std::min(kMaxFramesPerLaunch, n_cams - f0);
+        int tiles = 0;
+        for (int j = 0; j < nf; ++j) {
+            const fnr_camera *cam = &cams[f0 + j];
+            fill_frame(&a.f[j], cam, rgba_dev + pix_off * 4, stats_dev ? stats_dev + pix_off : nullptr,
+                       debug_cells_dev ? debug_cells_dev + pix_off * rc.N : nullptr, tiles);
+            tiles += frame_tiles(cam);
+            pix_off += int64_t(cam->width) * cam->height;
+        }
+        a.n_frames = nf;
+        a.total_tiles = tiles;
+        if ((e = launch_march(a, s)) != cudaSuccess) return cuda_fail(e, "march launch");
+    }
+    return FNR_OK;
+}
+
+}  // extern "C"

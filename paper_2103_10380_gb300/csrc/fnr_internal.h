@@ -1,0 +1,100 @@
+// fnr_internal.h -- structures shared by libfnr's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <set>
+#include <string>
+
+#include "fnr.h"
+
+namespace fnr {
+
+// Read-only view of one cache's device data, passed to kernels by value.
+struct CacheView {
+    const void *sigma;    // [k^3] stored density
+    const char *uvw;      // [k^3] records, rec_stride bytes apart
+    const void *beta;     // [l*l][D] stored weights
+    const float *ct;      // [l] cos(theta_j) boundaries
+    const float *qp;      // [l] azimuth-key boundaries
+    const float *scales;  // FP8: [1 + 3D]
+    float bmin[3];
+    float scale[3];       // binary32(k / (bmax - bmin)) per axis
+    float kf;             // (float)k
+    int32_t k, D, l;
+    int32_t rec_stride;   // bytes
+    int32_t pos_prec, dir_prec;
+};
+
+// Per-launch constants of one render request.
+struct RenderConst {
+    int32_t N;
+    float t_near;
+    float dt;             // Delta, binary32
+    int32_t act;
+    long long s_thr;      // termination threshold on the fixed-point optical depth
+    float bg[3];
+    int32_t pad;
+};
+
+// One view inside a launch. Tiles are 8 x 4 pixels, one warp each.
+struct FrameDesc {
+    float c2w[12];
+    float fx, fy, cx, cy;
+    int32_t W, H;
+    int32_t tiles_x;
+    int32_t tile_begin;   // first launch-global tile of this frame
+    float *rgba;          // [H*W][4]
+    fnr_ray_stats *stats; // [H*W] or null
+    int32_t *cells;       // [H*W][N] or null
+};
+
+constexpr int kTileW = 8, kTileH = 4;
+constexpr int kMaxFramesPerLaunch = 32;
+
+struct MarchArgs {
+    CacheView c;
+    RenderConst r;
+    int32_t n_frames;
+    int32_t total_tiles;
+    FrameDesc f[kMaxFramesPerLaunch];
+};
+
+// Host-side helpers shared by the API and the kernels' launchers.
+int rec_stride_bytes(int prec, int D);
+size_t elem_bytes(int prec);
+
+// Launchers (march.cu / quant.cu). Return cudaError_t of the launch.
+cudaError_t launch_march(const MarchArgs &a, cudaStream_t s);
+cudaError_t launch_convert_sigma(const float *in, void *out, int64_t n, int prec, const float *scale,
+                                 cudaStream_t s);
+cudaError_t launch_convert_uvw(const float *in, char *out, int64_t n_cells, int D, int prec, int rec_stride,
+                               const float *scales, cudaStream_t s);
+cudaError_t launch_convert_beta(const float *in, void *out, int64_t n, int prec, cudaStream_t s);
+cudaError_t launch_absmax(const float *sigma, const float *uvw, int64_t n_cells, int nch, unsigned *amax_bits,
+                          cudaStream_t s);
+cudaError_t launch_scales_from_absmax(const unsigned *amax_bits, float *scales, int n, cudaStream_t s);
+
+}  // namespace fnr
+
+struct fnr_cache {
+    fnr_cache_desc desc;
+    void *base = nullptr;
+    bool owned = true;
+    uint64_t footprint = 0;
+    fnr::CacheView view;
+    std::atomic<int> inflight{0};
+    fnr_context *ctx = nullptr;
+};
+
+struct fnr_context {
+    int device = 0;
+    int num_sms = 0;
+    uint64_t budget = 0;
+    std::atomic<uint64_t> used{0};
+    std::mutex mu;
+    std::set<fnr_cache *> caches;
+};

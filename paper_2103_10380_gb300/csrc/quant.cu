@@ -1,0 +1,132 @@
+// quant.cu -- cache storage conversion: binary32 source arrays -> FP32 / FP16 /
+// FP8-E4M3 cache records, with per-channel FP8 scales from a device absmax.
+//
+// Densities are clamped to >= 0 (NaN -> 0) before storage. FP16 rounds to
+// nearest even; FP8 stores E4M3(x / scale_c) rounded to nearest even and
+// saturated to +-448, scale_c = absmax_c / 448 (binary32 division; 1 for an
+// all-zero channel). The (u, v, w) records are padded to rec_stride bytes with
+// zeros so every record starts on a 16-byte (FP8: 8-byte) boundary.
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "fnr_internal.h"
+
+namespace fnr {
+
+namespace {
+
+__device__ __forceinline__ float clamp_density(float v) { return v > 0.0f ? v : 0.0f; }
+
+__device__ __forceinline__ unsigned char to_e4m3(float v) {
+    return static_cast<unsigned char>(__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3));
+}
+
+unsigned grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 152 * 64) b = 152 * 64;
+    return static_cast<unsigned>(b < 1 ? 1 : b);
+}
+
+__global__ void convert_sigma_kernel(const float *__restrict__ in, void *__restrict__ out, int64_t n, int prec,
+                                     const float *__restrict__ scale) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = clamp_density(in[i]);
+        if (prec == FNR_PREC_FP32) static_cast<float *>(out)[i] = v;
+        else if (prec == FNR_PREC_FP16) static_cast<__half *>(out)[i] = __float2half_rn(v);
+        else static_cast<unsigned char *>(out)[i] = to_e4m3(__fdiv_rn(v, scale[0]));
+    }
+}
+
+// One thread per output byte-group would waste bandwidth on the padding; one
+// thread per (cell, channel) element, padding written by channel-0 threads.
+__global__ void convert_uvw_kernel(const float *__restrict__ in, char *__restrict__ out, int64_t n_cells, int nch,
+                                   int prec, int rec_stride, const float *__restrict__ scales) {
+    const int64_t total = n_cells * nch;
+    const int es = prec == FNR_PREC_FP32 ? 4 : prec == FNR_PREC_FP16 ? 2 : 1;
+    const int pad_bytes = rec_stride - nch * es;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cell = e / nch;
+        const int ch = static_cast<int>(e - cell * nch);
+        char *rec = out + cell * rec_stride;
+        const float v = in[e];
+        if (prec == FNR_PREC_FP32) reinterpret_cast<float *>(rec)[ch] = v;
+        else if (prec == FNR_PREC_FP16) reinterpret_cast<__half *>(rec)[ch] = __float2half_rn(v);
+        else reinterpret_cast<unsigned char *>(rec)[ch] = to_e4m3(__fdiv_rn(v, scales[1 + ch]));
+        if (ch == 0)
+            for (int b = 0; b < pad_bytes; ++b) rec[nch * es + b] = 0;
+    }
+}
+
+__global__ void convert_beta_kernel(const float *__restrict__ in, void *__restrict__ out, int64_t n, int prec) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (prec == FNR_PREC_FP16) static_cast<__half *>(out)[i] = __float2half_rn(in[i]);
+        else static_cast<float *>(out)[i] = in[i];
+    }
+}
+
+// Channel absmax: channel 0 = clamped density, 1..nch = (u, v, w) channels.
+// Non-negative binary32 values order like their bit patterns, so an unsigned
+// atomicMax on the bits is an exact max. NaNs are skipped.
+__global__ void absmax_kernel(const float *__restrict__ sigma, const float *__restrict__ uvw, int64_t n_cells, int nch,
+                              unsigned *__restrict__ amax_bits) {
+    __shared__ unsigned smax[1 + 3 * FNR_MAX_D];
+    for (int c = threadIdx.x; c <= nch; c += blockDim.x) smax[c] = 0u;
+    __syncthreads();
+    unsigned local_s = 0u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_cells; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = fabsf(clamp_density(sigma[i]));
+        local_s = max(local_s, __float_as_uint(v));
+    }
+    atomicMax(&smax[0], local_s);
+    const int64_t total = n_cells * nch;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const float v = fabsf(uvw[e]);
+        if (v == v) atomicMax(&smax[1 + static_cast<int>(e % nch)], __float_as_uint(v));
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c <= nch; c += blockDim.x) atomicMax(&amax_bits[c], smax[c]);
+}
+
+__global__ void scales_kernel(const unsigned *__restrict__ amax_bits, float *__restrict__ scales, int n) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) {
+        const float a = __uint_as_float(amax_bits[c]);
+        scales[c] = a > 0.0f ? __fdiv_rn(a, 448.0f) : 1.0f;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_convert_sigma(const float *in, void *out, int64_t n, int prec, const float *scale, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    convert_sigma_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, out, n, prec, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_uvw(const float *in, char *out, int64_t n_cells, int D, int prec, int rec_stride,
+                               const float *scales, cudaStream_t s) {
+    if (n_cells <= 0) return cudaSuccess;
+    convert_uvw_kernel<<<grid_for(n_cells * 3 * D, 256), 256, 0, s>>>(in, out, n_cells, 3 * D, prec, rec_stride,
+                                                                        scales);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_beta(const float *in, void *out, int64_t n, int prec, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    convert_beta_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, out, n, prec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(const float *sigma, const float *uvw, int64_t n_cells, int nch, unsigned *amax_bits,
+                          cudaStream_t s) {
+    if (n_cells <= 0) return cudaSuccess;
+    absmax_kernel<<<grid_for(n_cells * nch, 256), 256, 0, s>>>(sigma, uvw, n_cells, nch, amax_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scales_from_absmax(const unsigned *amax_bits, float *scales, int n, cudaStream_t s) {
+    scales_kernel<<<1, 64, 0, s>>>(amax_bits, scales, n);
+    return cudaGetLastError();
+}
+
+}  // namespace fnr

@@ -1,0 +1,81 @@
+"""Host-side checks of the C ABI: the library loads, exports every declared
+symbol, and its pure size functions agree with the paper's printed integers.
+No CUDA compute is issued here."""
+
+import json
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fnr():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2103_10380_gb300 as fnr
+    return fnr
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"FNR_API\s+[\w\s\*]*?\b(fnr_\w+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol(fnr):
+    import ctypes
+    names = declared_symbols()
+    assert len(names) >= 10
+    L = ctypes.CDLL(fnr.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(L, n), f"{n} declared in include/ but not exported"
+    # the binding knows every declared symbol, with its signature
+    assert names <= set(fnr.SIGNATURES), names - set(fnr.SIGNATURES)
+
+
+def test_struct_sizes_match_header(fnr):
+    import ctypes
+    assert ctypes.sizeof(fnr.fnr_cache_desc) == 48
+    assert ctypes.sizeof(fnr.fnr_camera) == 72
+    assert ctypes.sizeof(fnr.fnr_render_params) == 32
+    assert ctypes.sizeof(fnr.fnr_ray_stats) == 16
+
+
+def test_cache_bytes_paper_integers(fnr):
+    """fnr_cache_bytes follows the supplementary cache-size formula (second version)."""
+    with open(os.path.join(ROOT, "tests", "golden", "cache_sizes.json")) as f:
+        cases = {c["formula"]: c for c in json.load(f)["cases"]}
+    c = cases["fastnerf"]
+    d = fnr.make_desc(c["k"], c["D"], c["l"], fnr.FNR_PREC_FP16, fnr.FNR_PREC_FP16)
+    assert fnr.fnr_cache_bytes(d) == c["pos_bytes"] + c["dir_bytes"]
+    # FP32 storage doubles every term; FP8 halves the position cache and adds 25 scales
+    d32 = fnr.make_desc(1024, 8, 1024, fnr.FNR_PREC_FP32, fnr.FNR_PREC_FP32)
+    assert fnr.fnr_cache_bytes(d32) == 2 * (c["pos_bytes"] + c["dir_bytes"])
+    d8 = fnr.make_desc(1024, 8, 1024, fnr.FNR_PREC_FP8_E4M3, fnr.FNR_PREC_FP16)
+    assert fnr.fnr_cache_bytes(d8) == c["pos_bytes"] // 2 + c["dir_bytes"] + 25 * 4
+
+
+def test_cache_footprint_and_invalid_desc(fnr):
+    d = fnr.make_desc(512, 8, 512, fnr.FNR_PREC_FP32, fnr.FNR_PREC_FP32)
+    # 512^3 * (4 + 96) + tables: the 100-byte records already sit on 16-byte boundaries
+    assert fnr.fnr_cache_footprint(d) >= 512 ** 3 * 100 + 512 * 512 * 8 * 4
+    assert fnr.fnr_cache_footprint(d) - fnr.fnr_cache_bytes(d) < 1 << 16
+    d6 = fnr.make_desc(64, 6, 64, fnr.FNR_PREC_FP32, fnr.FNR_PREC_FP32)  # 72-byte triples padded to 80
+    assert fnr.fnr_cache_footprint(d6) >= 64 ** 3 * (4 + 80)
+    for bad in (fnr.make_desc(0, 8, 64), fnr.make_desc(64, 17, 64), fnr.make_desc(64, 8, 1),
+                fnr.make_desc(64, 8, 64, 7), fnr.make_desc(64, 8, 64, bmin=(0, 0, 0), bmax=(1, 0, 1))):
+        assert fnr.fnr_cache_bytes(bad) == 0 and fnr.fnr_cache_footprint(bad) == 0
+
+
+def test_null_arguments_rejected_without_gpu(fnr):
+    L = fnr.lib()
+    assert L.fnr_context_create(0, 0, None) == fnr.FNR_ERR_INVALID_ARG
+    assert b"NULL" in L.fnr_last_error()
+    assert L.fnr_render(None, None, None, 0, None, None, None, None, None) == fnr.FNR_ERR_INVALID_ARG
+    assert L.fnr_context_destroy(None) == fnr.FNR_OK
