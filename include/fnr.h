@@ -31,10 +31,12 @@
  *      dcx = ((px + 0.5) - cx) / fx,  dcy = -(((py + 0.5) - cy) / fy)
  *      w_r = fma(R_r0, dcx, fma(R_r1, dcy, -R_r2)), r = 0, 1, 2 (c2w rotation)
  *      n2 = fma(wx, wx, fma(wy, wy, wz * wz)), d = w / sqrt(n2), o = c2w eye.
- *  - Samples (Section 3.1, N midpoints on [t_near, t_far], delta_i = Delta):
- *      Delta = (t_far - t_near) / N, t_i = fma(i + 0.5, Delta, t_near),
- *      p = fma(t_i, d, o), g_a = (p_a - bmin_a) * s_a with
- *      s_a = binary32(k / (bmax_a - bmin_a)) evaluated in FP64.
+ *  - Samples (Section 3.1, N midpoints t_i = t_near + (i + 0.5) Delta on
+ *    [t_near, t_far], delta_i = Delta = (t_far - t_near) / N). The grid
+ *    coordinates g_a = (o_a + t_i d_a - bmin_a) s_a, s_a = binary32(k / (bmax_a -
+ *    bmin_a)) evaluated in FP64, are computed as the affine map in i:
+ *      u_a = d_a * s_a, e_a = u_a * Delta, f_a = fma(t_near, u_a, (o_a - bmin_a) * s_a),
+ *      g_a(i) = fma(i + 0.5, e_a, f_a).
  *    The sample is inside the cache iff 0 <= g_a < k on all axes; its cell is
  *    floor(g) and its linear index (z * k + y) * k + x (Section 3.3, cell-
  *    centred grid, nearest neighbour as in Section 4).
@@ -96,7 +98,7 @@ typedef int32_t fnr_status;
 #define FNR_LOC_DEVICE 1
 
 #define FNR_MAX_D 16
-#define FNR_MAX_K 2048
+#define FNR_MAX_K 1290 /* k^3 < 2^31: cell indices are int32 */
 #define FNR_MAX_L 4096
 #define FNR_MAX_SAMPLES 4096
 #define FNR_MAX_IMAGE_SIDE 16384
@@ -226,7 +228,7 @@ typedef struct {
  *   rgba_dev        float[P][4], (R, G, B, alpha) at P_f + py * W_f + px
  *   stats_dev       fnr_ray_stats[P] or NULL
  *   debug_cells_dev int32[P][n_samples] or NULL: per sample its cell index,
- *                   -1 outside the box, -2 after termination (needs k^3 < 2^31).
+ *                   -1 outside the box, -2 after termination.
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
 FNR_API fnr_status fnr_render(fnr_context *ctx, const fnr_cache *cache, const fnr_camera *cams, int32_t n_cams,
                       const fnr_render_params *params, float *rgba_dev, fnr_ray_stats *stats_dev,

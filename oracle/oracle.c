@@ -318,13 +318,22 @@ static void render_ray(const ray_ctx *X, int32_t px, int32_t py, double *rgba, i
     int32_t n_steps = N, n_look = 0, n_occ = 0;
     double uvw[48];
     const float kf = (float)k;
+    /* Cell coordinates of sample i: g_a = (o_a + t_i d_a - bmin_a) s_a with
+     * t_i = near + (i + 1/2) Delta, evaluated in binary32 as
+     * g_a = fma(i + 1/2, e_a, f_a), e_a = (d_a s_a) Delta,
+     * f_a = fma(near, d_a s_a, (o_a - bmin_a) s_a). */
+    float e[3], f[3];
+    for (int a = 0; a < 3; ++a) {
+        float ua = d[a] * X->scale[a];
+        e[a] = ua * X->dt;
+        f[a] = fmaf(p->t_near, ua, (o[a] - c->bmin[a]) * X->scale[a]);
+    }
     for (int i = 0; i < N; ++i) {
-        float t = fmaf((float)i + 0.5f, X->dt, p->t_near);
+        float fi = (float)i + 0.5f;
         float g[3];
         int inside = 1;
         for (int a = 0; a < 3; ++a) {
-            float pa = fmaf(t, d[a], o[a]);
-            g[a] = (pa - c->bmin[a]) * X->scale[a];
+            g[a] = fmaf(fi, e[a], f[a]);
             if (!(g[a] >= 0.0f && g[a] < kf)) inside = 0;
         }
         if (!inside) {

@@ -441,8 +441,6 @@ fnr_status fnr_render(fnr_context *ctx, const fnr_cache *cache, const fnr_camera
     if (st != FNR_OK) return st;
     for (int i = 0; i < n_cams; ++i)
         if ((st = check_camera(&cams[i])) != FNR_OK) return st;
-    if (debug_cells_dev && uint64_t(cache->desc.k) * cache->desc.k * cache->desc.k >= (uint64_t(1) << 31))
-        return fail(FNR_ERR_UNSUPPORTED, "debug cells need k^3 < 2^31");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -44,7 +44,7 @@ def device_bytes(ptr: int, nbytes: int):
     import torch
 
     class _View:
-        __cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, True), "version": 3}
+        __cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False), "version": 3}
 
     return torch.as_tensor(_View(), device="cuda").cpu().numpy()
 

@@ -92,8 +92,12 @@ def test_homogeneous_box_closed_form(sigma0, expect_steps):
         elif i < 8 or i > 55:
             assert cells[0, i] == -1
         else:
-            iz = math.floor((z + 1.5) * 64 / 3)
-            assert cells[0, i] == (iz * k + 32) * k + 32
+            gz = (z + 1.5) * 64 / 3  # exact: z is a multiple of 1/32
+            iz = math.floor(gz)
+            ok = {(iz * k + 32) * k + 32}
+            if abs(gz - round(gz)) < 1e-9:  # sample exactly on a cell face: binary32 rounding picks a side
+                ok.add(((round(gz) - 1) * k + 32) * k + 32)
+            assert cells[0, i] in ok
 
 
 def test_homogeneous_box_chord_form():
