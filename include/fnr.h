@@ -234,6 +234,65 @@ FNR_API fnr_status fnr_render(fnr_context *ctx, const fnr_cache *cache, const fn
                       const fnr_render_params *params, float *rgba_dev, fnr_ray_stats *stats_dev,
                       int32_t *debug_cells_dev, fnr_stream_t stream);
 
+
+/* ------------------------------------------------------------------ serving */
+/* A request for one view (Section 4's per-view render, served). The request
+ * is copied at submit; rgba_dev / stats_dev stay caller-owned and must stay
+ * valid until the request has completed. The cache cannot be freed while one
+ * of its requests is queued or in flight.
+ * Ordering: the launch that renders the request first waits for all work that
+ * was queued on `stream` when fnr_submit was called (NULL: the legacy default
+ * stream), so outputs prepared on that stream are not overwritten. After
+ * fnr_poll / fnr_wait report completion the outputs may be read on any stream. */
+typedef struct {
+    const fnr_cache *cache;
+    fnr_camera camera;
+    fnr_render_params params;
+    float *rgba_dev;          /* float[H*W][4] */
+    fnr_ray_stats *stats_dev; /* [H*W] or NULL */
+    fnr_stream_t stream;      /* the producer stream of the outputs (see above) */
+    int32_t priority;         /* reserved, must be 0 */
+    int32_t reserved;
+} fnr_request;
+
+typedef struct {
+    fnr_status status;        /* FNR_OK, or the error that ended the request */
+    int32_t reserved;
+    uint64_t t_submit_ns;     /* steady-clock nanoseconds */
+    uint64_t t_admit_ns;      /* 0 while queued */
+    uint64_t t_done_ns;       /* when the host saw the completion word */
+    uint64_t n_rays;
+    int64_t batch;            /* launch the request ran in (-1 while queued) */
+    uint64_t ticket;
+} fnr_result;
+
+typedef struct {
+    int32_t queue_capacity;     /* queued requests before FNR_ERR_QUEUE_FULL (0: 4096) */
+    int32_t max_batch_requests; /* requests per persistent launch, <= 64 (0: 64) */
+    int64_t max_batch_rays;     /* rays per launch (0: 16 Mi) */
+    int32_t n_slots;            /* launches in flight at once, <= 8 (0: 3) */
+    int32_t use_graphs;         /* 1: each slot replays a captured CUDA graph */
+} fnr_serve_config;
+
+/* Start the request loop (a host scheduler thread plus n_slots streams).
+ * fnr_submit starts it with the defaults if it is not running.
+ * Errors: INVALID_ARG (already running, bad config), CUDA. */
+FNR_API fnr_status fnr_serve_start(fnr_context *ctx, const fnr_serve_config *cfg);
+/* Drain queued and in-flight requests, then stop the loop. */
+FNR_API fnr_status fnr_serve_stop(fnr_context *ctx);
+/* Queue one request; returns at once with a ticket. Requests are admitted in
+ * arrival order into persistent launches as slots free up and as the HBM
+ * budget allows (each admitted request charges its output bytes until it
+ * completes). Errors: INVALID_ARG, UNSUPPORTED (D not served), BUDGET (the
+ * output alone exceeds the budget), QUEUE_FULL. */
+FNR_API fnr_status fnr_submit(fnr_context *ctx, const fnr_request *req, uint64_t *ticket);
+/* FNR_ERR_NOT_READY while queued or in flight (out is filled with the times so
+ * far); otherwise fills out, forgets the ticket and returns FNR_OK (the
+ * request's own outcome is out->status). INVALID_ARG for an unknown ticket. */
+FNR_API fnr_status fnr_poll(fnr_context *ctx, uint64_t ticket, fnr_result *out);
+/* As fnr_poll, blocking up to timeout_ms; FNR_ERR_TIMEOUT if still not done. */
+FNR_API fnr_status fnr_wait(fnr_context *ctx, uint64_t ticket, uint32_t timeout_ms, fnr_result *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,23 @@ class fnr_ray_stats(ctypes.Structure):
                 ("dir_cell", ctypes.c_int32)]
 
 
+class fnr_request(ctypes.Structure):
+    _fields_ = [("cache", ctypes.c_void_p), ("camera", fnr_camera), ("params", fnr_render_params),
+                ("rgba_dev", ctypes.c_void_p), ("stats_dev", ctypes.c_void_p), ("stream", ctypes.c_void_p),
+                ("priority", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class fnr_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("t_submit_ns", ctypes.c_uint64),
+                ("t_admit_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64), ("n_rays", ctypes.c_uint64),
+                ("batch", ctypes.c_int64), ("ticket", ctypes.c_uint64)]
+
+
+class fnr_serve_config(ctypes.Structure):
+    _fields_ = [("queue_capacity", ctypes.c_int32), ("max_batch_requests", ctypes.c_int32),
+                ("max_batch_rays", ctypes.c_int64), ("n_slots", ctypes.c_int32), ("use_graphs", ctypes.c_int32)]
+
+
 # Every symbol include/fnr.h declares, with (argtypes, restype).
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -100,6 +117,11 @@ SIGNATURES = {
     "fnr_cache_get_layout": ([_P, ctypes.POINTER(fnr_cache_layout)], ctypes.c_int32),
     "fnr_render": ([_P, _P, ctypes.POINTER(fnr_camera), ctypes.c_int32, ctypes.POINTER(fnr_render_params), _P, _P,
                     _P, _P], ctypes.c_int32),
+    "fnr_serve_start": ([_P, ctypes.POINTER(fnr_serve_config)], ctypes.c_int32),
+    "fnr_serve_stop": ([_P], ctypes.c_int32),
+    "fnr_submit": ([_P, ctypes.POINTER(fnr_request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int32),
+    "fnr_poll": ([_P, ctypes.c_uint64, ctypes.POINTER(fnr_result)], ctypes.c_int32),
+    "fnr_wait": ([_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(fnr_result)], ctypes.c_int32),
 }
 
 _lib = None
@@ -227,3 +249,49 @@ def fnr_render(ctx: int, cache: int, cams, params: fnr_render_params, rgba, stat
     check(lib().fnr_render(ctx, cache, arr, len(cams), ctypes.byref(params), rgba.data_ptr(),
                            None if stats is None else stats.data_ptr(), None if cells is None else cells.data_ptr(),
                            _stream_handle(stream)))
+
+
+# ------------------------------------------------------------------ serving
+def fnr_serve_start(ctx: int, queue_capacity=0, max_batch_requests=0, max_batch_rays=0, n_slots=0,
+                    use_graphs=1):
+    cfg = fnr_serve_config(queue_capacity, max_batch_requests, max_batch_rays, n_slots, use_graphs)
+    check(lib().fnr_serve_start(ctx, ctypes.byref(cfg)))
+
+
+def fnr_serve_stop(ctx: int):
+    check(lib().fnr_serve_stop(ctx))
+
+
+def make_request(cache: int, cam, params: fnr_render_params, rgba, stats=None, stream=None) -> fnr_request:
+    """stream: the stream that produced rgba/stats (default: torch's current stream)."""
+    r = fnr_request()
+    r.cache = cache
+    r.camera = cam if isinstance(cam, fnr_camera) else make_camera(cam)
+    r.params = params
+    assert rgba.is_cuda and rgba.is_contiguous() and rgba.numel() >= 4 * r.camera.width * r.camera.height
+    r.rgba_dev = rgba.data_ptr()
+    r.stats_dev = None if stats is None else stats.data_ptr()
+    r.stream = _stream_handle(stream)
+    return r
+
+
+def fnr_submit(ctx: int, req: fnr_request) -> int:
+    t = ctypes.c_uint64()
+    check(lib().fnr_submit(ctx, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def fnr_poll(ctx: int, ticket: int):
+    """Returns fnr_result when done, None while queued or in flight."""
+    out = fnr_result()
+    st = lib().fnr_poll(ctx, ticket, ctypes.byref(out))
+    if st == FNR_ERR_NOT_READY:
+        return None
+    check(st)
+    return out
+
+
+def fnr_wait(ctx: int, ticket: int, timeout_ms: int = 10000) -> fnr_result:
+    out = fnr_result()
+    check(lib().fnr_wait(ctx, ticket, timeout_ms, ctypes.byref(out)))
+    return out

@@ -99,7 +99,7 @@ static void bin_tables(int l, std::vector<float> &ct, std::vector<float> &qp) {
     }
 }
 
-static bool charge(fnr_context *ctx, uint64_t bytes) {
+bool budget_charge(fnr_context *ctx, uint64_t bytes) {
     uint64_t cur = ctx->used.load();
     for (;;) {
         if (ctx->budget && cur + bytes > ctx->budget) return false;
@@ -107,7 +107,7 @@ static bool charge(fnr_context *ctx, uint64_t bytes) {
     }
 }
 
-static void uncharge(fnr_context *ctx, uint64_t bytes) { ctx->used.fetch_sub(bytes); }
+void budget_uncharge(fnr_context *ctx, uint64_t bytes) { ctx->used.fetch_sub(bytes); }
 
 // RAII device buffer for build-time temporaries.
 struct DevBuf {
@@ -305,6 +305,10 @@ fnr_status fnr_context_create(int32_t device, uint64_t hbm_budget_bytes, fnr_con
 fnr_status fnr_context_destroy(fnr_context *ctx) {
     clear_error();
     if (!ctx) return FNR_OK;
+    {
+        std::lock_guard<std::mutex> g(ctx->serve_mu);
+        server_stop(ctx);  // drains queued and in-flight requests
+    }
     cudaSetDevice(ctx->device);
     std::set<fnr_cache *> cs;
     {
@@ -352,7 +356,7 @@ fnr_status fnr_build_cache(fnr_context *ctx, const fnr_cache_desc *desc, const f
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     const Layout L = layout_of(desc);
-    if (!charge(ctx, L.total))
+    if (!budget_charge(ctx, L.total))
         return fail(FNR_ERR_BUDGET, "cache needs %llu bytes, budget %llu, in use %llu", (unsigned long long)L.total,
                     (unsigned long long)ctx->budget, (unsigned long long)ctx->used.load());
     fnr_cache *c = new fnr_cache();
@@ -360,7 +364,7 @@ fnr_status fnr_build_cache(fnr_context *ctx, const fnr_cache_desc *desc, const f
     c->footprint = L.total;
     c->ctx = ctx;
     if ((e = cudaMalloc(&c->base, L.total)) != cudaSuccess) {
-        uncharge(ctx, L.total);
+        budget_uncharge(ctx, L.total);
         delete c;
         return cuda_fail(e, "cache allocation");
     }
@@ -384,7 +388,7 @@ fnr_status fnr_build_cache(fnr_context *ctx, const fnr_cache_desc *desc, const f
     if (st == FNR_OK) st = build_from_arrays(c, src, L, s);
     if (st != FNR_OK) {
         cudaFree(c->base);
-        uncharge(ctx, L.total);
+        budget_uncharge(ctx, L.total);
         delete c;
         return st;
     }
@@ -408,7 +412,7 @@ fnr_status fnr_cache_free(fnr_context *ctx, fnr_cache *c) {
     }
     cudaSetDevice(ctx->device);
     if (c->owned && c->base) cudaFree(c->base);
-    uncharge(ctx, c->footprint);
+    budget_uncharge(ctx, c->footprint);
     delete c;
     return FNR_OK;
 }

@@ -78,6 +78,9 @@ cudaError_t launch_absmax(const float *sigma, const float *uvw, int64_t n_cells,
                           cudaStream_t s);
 cudaError_t launch_scales_from_absmax(const unsigned *amax_bits, float *scales, int n, cudaStream_t s);
 
+struct Server;
+void server_stop(fnr_context *ctx);
+
 }  // namespace fnr
 
 struct fnr_cache {
@@ -97,4 +100,6 @@ struct fnr_context {
     std::atomic<uint64_t> used{0};
     std::mutex mu;
     std::set<fnr_cache *> caches;
+    std::mutex serve_mu;
+    fnr::Server *server = nullptr;
 };

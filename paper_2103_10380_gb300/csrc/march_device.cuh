@@ -1,0 +1,558 @@
+// march_device.cuh -- device code of the cached ray march, shared by the
+// plain render kernel (march.cu) and the persistent serving kernel (serve.cu).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "fnr_internal.h"
+
+namespace fnr {
+namespace dev {
+
+
+// Tuning knobs (defaults are the measured best; see the design notes):
+//   FNR_UNROLL    density loads issued together per lane
+//   FNR_BLOCK / FNR_MINB  threads per block / minimum resident blocks per SM
+//   FNR_FAST_EXP  1: exponentials of the occupied-sample path via ex2.approx
+//   FNR_QUEUE     1: lanes march density only and queue occupied samples; the
+//                 warp shades 32 queued samples at a time (march_tile_queued)
+#ifndef FNR_UNROLL
+#define FNR_UNROLL 8
+#endif
+#ifndef FNR_BLOCK
+#define FNR_BLOCK 128
+#endif
+#ifndef FNR_MINB
+#define FNR_MINB 8
+#endif
+#ifndef FNR_FAST_EXP
+#define FNR_FAST_EXP 1
+#endif
+#ifndef FNR_QUEUE
+#define FNR_QUEUE 1
+#endif
+constexpr int kUnroll = FNR_UNROLL;
+
+__device__ __forceinline__ float e4m3_to_float(unsigned int byte) {
+    __half_raw h = __nv_cvt_fp8_to_halfraw(static_cast<__nv_fp8_storage_t>(byte), __NV_E4M3);
+    return __half2float(__half(h));
+}
+
+template <int PREC, int D>
+struct Record;
+
+template <int D>
+struct Record<FNR_PREC_FP32, D> {
+    static constexpr int NV = (3 * D + 3) / 4;
+    float4 v[NV];
+    __device__ __forceinline__ void load(const char *p) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = __ldg(reinterpret_cast<const float4 *>(p) + j);
+    }
+    __device__ __forceinline__ float get(int i) const {
+        const float4 &q = v[i >> 2];
+        return (i & 3) == 0 ? q.x : (i & 3) == 1 ? q.y : (i & 3) == 2 ? q.z : q.w;
+    }
+};
+
+template <int D>
+struct Record<FNR_PREC_FP16, D> {
+    static constexpr int NV = (6 * D + 15) / 16;
+    uint4 v[NV];
+    __device__ __forceinline__ void load(const char *p) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = __ldg(reinterpret_cast<const uint4 *>(p) + j);
+    }
+    __device__ __forceinline__ float get(int i) const {
+        const uint4 &q = v[i >> 3];
+        const int w = (i >> 1) & 3;
+        unsigned int word = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
+        unsigned short bits = static_cast<unsigned short>((i & 1) ? (word >> 16) : (word & 0xffffu));
+        return __half2float(__ushort_as_half(bits));
+    }
+};
+
+template <int D>
+struct Record<FNR_PREC_FP8_E4M3, D> {
+    static constexpr int NV = (3 * D + 7) / 8;
+    uint2 v[NV];
+    __device__ __forceinline__ void load(const char *p) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = __ldg(reinterpret_cast<const uint2 *>(p) + j);
+    }
+    __device__ __forceinline__ float get(int i) const {
+        const uint2 &q = v[i >> 3];
+        unsigned int word = ((i >> 2) & 1) ? q.y : q.x;
+        return e4m3_to_float((word >> (8 * (i & 3))) & 0xffu);
+    }
+};
+
+template <int PREC>
+__device__ __forceinline__ float load_sigma(const CacheView &c, int cell, float sigma_scale) {
+    if constexpr (PREC == FNR_PREC_FP32) {
+        return __ldg(static_cast<const float *>(c.sigma) + cell);
+    } else if constexpr (PREC == FNR_PREC_FP16) {
+        return __half2float(__ldg(static_cast<const __half *>(c.sigma) + cell));
+    } else {
+        unsigned int q = __ldg(static_cast<const unsigned char *>(c.sigma) + cell);
+        return __fmul_rn(e4m3_to_float(q), sigma_scale);  // binary32 dequantisation
+    }
+}
+
+// floor(s * 2^32) for binary32 s, by integer shifts of the significand (no
+// float -> int64 conversion: on this GPU those run on the FP64 pipe).
+// s <= 0 or NaN -> 0; s >= 2^31 -> 2^63 - 1 (saturated).
+__device__ __forceinline__ long long fixed_depth(float s) {
+    if (!(s > 0.0f)) return 0;
+    if (s >= 2147483648.0f) return 0x7fffffffffffffffLL;
+    const unsigned int bits = __float_as_uint(s);
+    const int ex = static_cast<int>((bits >> 23) & 0xffu);
+    const unsigned long long mant = (bits & 0x7fffffu) | (ex ? 0x800000u : 0u);
+    const int shift = (ex ? ex - 127 : -126) - 23 + 32;  // s * 2^32 = mant * 2^shift
+    if (shift >= 0) return static_cast<long long>(mant << shift);
+    return -shift >= 64 ? 0 : static_cast<long long>(mant >> (-shift));
+}
+
+// Azimuth key in [0, 4], monotone in atan2(y, x) wrapped to [0, 2 pi).
+__device__ __forceinline__ float phi_key(float x, float y) {
+    if (x == 0.0f && y == 0.0f) return 0.0f;
+    if (y >= 0.0f) {
+        if (x >= 0.0f) return __fdiv_rn(y, __fadd_rn(x, y));
+        return __fadd_rn(1.0f, __fdiv_rn(-x, __fadd_rn(y, -x)));
+    }
+    if (x < 0.0f) return __fadd_rn(2.0f, __fdiv_rn(-y, __fadd_rn(-x, -y)));
+    return __fadd_rn(3.0f, __fdiv_rn(x, __fadd_rn(x, -y)));
+}
+
+// Direction cell: counts of boundaries passed; the libm estimate only picks
+// where the exact walk over the (monotone) tables starts.
+__device__ __forceinline__ int dir_cell(const CacheView &c, float dx, float dy, float dz) {
+    const int l = c.l;
+    const float inv_pi = 0.318309886183790671538f;
+    int it = static_cast<int>(acosf(fminf(fmaxf(dz, -1.0f), 1.0f)) * inv_pi * static_cast<float>(l));
+    it = min(max(it, 0), l - 1);
+    while (it < l - 1 && dz <= __ldg(c.ct + it + 1)) ++it;
+    while (it > 0 && dz > __ldg(c.ct + it)) --it;
+    float ph = atan2f(dy, dx);
+    if (ph < 0.0f) ph += 6.28318530717958647692f;
+    int ip = static_cast<int>(ph * (0.5f * inv_pi) * static_cast<float>(l));
+    ip = min(max(ip, 0), l - 1);
+    const float q = phi_key(dx, dy);
+    while (ip < l - 1 && q >= __ldg(c.qp + ip + 1)) ++ip;
+    while (ip > 0 && q < __ldg(c.qp + ip)) --ip;
+    return it * l + ip;
+}
+
+// Per-ray setup shared by both march variants: a1 (ray), a2 (direction cell
+// and beta), and the per-ray affine coefficients of the sample cells with the
+// sample range that can reach the box.
+template <int PREC, int D>
+struct RaySetup {
+    static constexpr int NB = (PREC == FNR_PREC_FP8_E4M3) ? 3 * D : D;
+    float bw[NB];  // beta (FP8: beta_i * scale of channel (ch, i))
+    float e[3], f[3];
+    int i_lo, i_hi;
+    int dcell;
+    float sigma_scale;
+
+    __device__ __forceinline__ void init(const CacheView &c, const RenderConst &r, const FrameDesc &F, int px,
+                                         int py) {
+        // a1: ray (binary32, fixed sequence)
+        const float dcx = __fdiv_rn(__fsub_rn(__fadd_rn(static_cast<float>(px), 0.5f), F.cx), F.fx);
+        const float dcy = -__fdiv_rn(__fsub_rn(__fadd_rn(static_cast<float>(py), 0.5f), F.cy), F.fy);
+        const float wx = __fmaf_rn(F.c2w[0], dcx, __fmaf_rn(F.c2w[1], dcy, -F.c2w[2]));
+        const float wy = __fmaf_rn(F.c2w[4], dcx, __fmaf_rn(F.c2w[5], dcy, -F.c2w[6]));
+        const float wz = __fmaf_rn(F.c2w[8], dcx, __fmaf_rn(F.c2w[9], dcy, -F.c2w[10]));
+        const float n2 = __fmaf_rn(wx, wx, __fmaf_rn(wy, wy, __fmul_rn(wz, wz)));
+        const float len = __fsqrt_rn(n2);
+        const float dd[3] = {__fdiv_rn(wx, len), __fdiv_rn(wy, len), __fdiv_rn(wz, len)};
+        const float oo[3] = {F.c2w[3], F.c2w[7], F.c2w[11]};
+
+        // a2: direction cell and beta
+        dcell = dir_cell(c, dd[0], dd[1], dd[2]);
+        if constexpr (PREC == FNR_PREC_FP8_E4M3) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                float b = c.dir_prec == FNR_PREC_FP16
+                              ? __half2float(__ldg(static_cast<const __half *>(c.beta) + (long long)dcell * D + i))
+                              : __ldg(static_cast<const float *>(c.beta) + (long long)dcell * D + i);
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) bw[ch * D + i] = b * __ldg(c.scales + 1 + ch * D + i);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+                bw[i] = c.dir_prec == FNR_PREC_FP16
+                            ? __half2float(__ldg(static_cast<const __half *>(c.beta) + (long long)dcell * D + i))
+                            : __ldg(static_cast<const float *>(c.beta) + (long long)dcell * D + i);
+        }
+        sigma_scale = (PREC == FNR_PREC_FP8_E4M3) ? __ldg(c.scales) : 1.0f;
+
+        // a3/a4 per ray: cell coordinates of sample i are g_a = fma(i + 1/2, e_a, f_a)
+        // with e_a = (d_a s_a) Delta and f_a = fma(near, d_a s_a, (o_a - bmin_a) s_a)
+        // (binary32, the order fixed in fnr.h).
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float ua = __fmul_rn(dd[a], c.scale[a]);
+            e[a] = __fmul_rn(ua, r.dt);
+            f[a] = __fmaf_rn(r.t_near, ua, __fmul_rn(__fsub_rn(oo[a], c.bmin[a]), c.scale[a]));
+        }
+        // Samples that can reach the box: a range widened by one cell on every face
+        // and two samples at each end, so every sample the exact test puts inside
+        // lies in [i_lo, i_hi); samples outside it are outside the box.
+        i_lo = 0;
+        i_hi = r.N;
+        const bool finite_dir = (dd[0] == dd[0]) && (dd[1] == dd[1]) && (dd[2] == dd[2]);
+        if (!finite_dir) i_hi = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (e[a] == 0.0f) {
+                if (!(f[a] >= -1.0f && f[a] <= c.kf + 1.0f)) i_hi = 0;
+            } else {
+                const float ta = (-1.0f - f[a]) / e[a] - 0.5f;
+                const float tb = (c.kf + 1.0f - f[a]) / e[a] - 0.5f;
+                const float lo = fmaxf(fminf(ta, tb) - 2.0f, -1.0f);
+                const float hi = fminf(fmaxf(ta, tb) + 2.0f, static_cast<float>(r.N) + 1.0f);
+                i_lo = max(i_lo, __float2int_rd(lo));
+                i_hi = min(i_hi, __float2int_ru(hi) + 1);
+            }
+        }
+        i_lo = min(i_lo, r.N);
+    }
+
+    // Cell of sample i (fi = i + 0.5) or -1 outside the box. For finite g,
+    // 0 <= g < k iff 0 <= floor(g) < k; floor goes straight to int32.
+    __device__ __forceinline__ int cell_of(const CacheView &c, float fi) const {
+        const float gx = __fmaf_rn(fi, e[0], f[0]);
+        const float gy = __fmaf_rn(fi, e[1], f[1]);
+        const float gz = __fmaf_rn(fi, e[2], f[2]);
+        const int ix = __float2int_rd(gx), iy = __float2int_rd(gy), iz = __float2int_rd(gz);
+        const unsigned int ku = static_cast<unsigned int>(c.k);
+        const bool in = static_cast<unsigned int>(ix) < ku && static_cast<unsigned int>(iy) < ku &&
+                        static_cast<unsigned int>(iz) < ku;
+        return in ? (iz * c.k + iy) * c.k + ix : -1;  // k^3 < 2^31
+    }
+
+    // a7: Eq. 5 and the activation for one record.
+    __device__ __forceinline__ void shade(const Record<PREC, D> &rec, int act, const float *b, float col[3]) const {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float x = 0.0f;
+#pragma unroll
+            for (int j = 0; j < D; ++j) x = __fmaf_rn(b[(PREC == FNR_PREC_FP8_E4M3) ? ch * D + j : j], rec.get(ch * D + j), x);
+#if FNR_FAST_EXP
+            col[ch] = act == FNR_ACT_IDENTITY ? x : __fdividef(1.0f, 1.0f + __expf(-x));
+#else
+            col[ch] = act == FNR_ACT_IDENTITY ? x : 1.0f / (1.0f + expf(-x));
+#endif
+        }
+    }
+};
+
+// exp(-od) and 1 - exp(-od) for the Eq. 1 update.
+__device__ __forceinline__ void extinction(float od, float &ext, float &alpha) {
+#if FNR_FAST_EXP
+    ext = __expf(-od);
+    alpha = 1.0f - ext;
+#else
+    ext = expf(-od);
+    alpha = -expm1f(-od);
+#endif
+}
+
+template <int PREC, int D>
+__device__ __forceinline__ void march_ray(const CacheView &c, const RenderConst &r, const FrameDesc &F, int px,
+                                          int py) {
+    RaySetup<PREC, D> R;
+    R.init(c, r, F, px, py);
+    const int i_lo = R.i_lo, i_hi = R.i_hi;
+    const float sigma_scale = R.sigma_scale;
+    float T = 1.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
+    long long S = 0;
+    int n_look = 0, n_occ = 0, n_steps = r.N;
+    const long long pix = static_cast<long long>(py) * F.W + px;
+    int32_t *cells_out = F.cells ? F.cells + pix * r.N : nullptr;
+    bool done = false;
+    if (cells_out)
+        for (int i = 0; i < i_lo; ++i) cells_out[i] = -1;
+    float fi = __fadd_rn(static_cast<float>(i_lo), 0.5f);  // i + 0.5, exact in binary32
+
+    // a3-a5 for one group: cells of samples i0 .. i0+U-1 and their density
+    // loads, all issued before any is consumed.
+    auto fill = [&](int i0, int (&cell)[kUnroll], float (&sg)[kUnroll]) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            cell[u] = (i0 + u < i_hi) ? R.cell_of(c, fi) : -1;
+            fi = __fadd_rn(fi, 1.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) sg[u] = cell[u] >= 0 ? load_sigma<PREC>(c, cell[u], sigma_scale) : 0.0f;
+    };
+    // a6-a8 for one group, in sample order, until termination.
+    auto consume = [&](int i0, const int (&cell)[kUnroll], const float (&sg)[kUnroll]) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int i = i0 + u;
+            if (i >= i_hi) break;
+            if (cells_out) cells_out[i] = cell[u];
+            if (cell[u] < 0) continue;
+            ++n_look;
+            const float s = sg[u];
+            if (!(s > 0.0f)) continue;
+            ++n_occ;
+            // a6: (u, v, w) record
+            Record<PREC, D> rec;
+            rec.load(c.uvw + static_cast<long long>(cell[u]) * c.rec_stride);
+            // a7: Eq. 5 and the activation
+            float col[3];
+            R.shade(rec, r.act, R.bw, col);
+            // a8: Eq. 1 and exact termination
+            const float od = __fmul_rn(s, r.dt);
+            float ext, alpha;
+            extinction(od, ext, alpha);
+            const float w = T * alpha;
+            Cr = __fmaf_rn(w, col[0], Cr);
+            Cg = __fmaf_rn(w, col[1], Cg);
+            Cb = __fmaf_rn(w, col[2], Cb);
+            T = T * ext;
+            const long long q = fixed_depth(s);
+            S = (S > 0x7fffffffffffffffLL - q) ? 0x7fffffffffffffffLL : S + q;
+            if (S >= r.s_thr) {
+                n_steps = i + 1;
+                done = true;
+                break;
+            }
+        }
+    };
+    for (int i0 = i_lo; i0 < i_hi && !done; i0 += kUnroll) {
+        int cell[kUnroll];
+        float sg[kUnroll];
+        fill(i0, cell, sg);
+        consume(i0, cell, sg);
+    }
+    if (cells_out) {
+        if (done)
+            for (int i = n_steps; i < r.N; ++i) cells_out[i] = -2;
+        else
+            for (int i = max(i_hi, i_lo); i < r.N; ++i) cells_out[i] = -1;
+    }
+    // a9: output
+    float4 o;
+    o.x = __fmaf_rn(T, r.bg[0], Cr);
+    o.y = __fmaf_rn(T, r.bg[1], Cg);
+    o.z = __fmaf_rn(T, r.bg[2], Cb);
+    o.w = 1.0f - T;
+    reinterpret_cast<float4 *>(F.rgba)[pix] = o;
+    if (F.stats) {
+        int4 st = make_int4(n_steps, n_look, n_occ, R.dcell);
+        reinterpret_cast<int4 *>(F.stats)[pix] = st;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Queued variant. The transmittance, the weights w_i = T_i alpha_i and the
+// termination step depend on the densities only, so each lane marches its ray
+// with density loads alone and appends (cell, w_i) of every occupied sample to
+// a per-warp queue in shared memory. Whenever 32 entries are queued the warp
+// shades them together -- 32 independent record loads in one round trip --
+// and every owner lane adds w_i * c_i to its colour in sample order, so the
+// binary32 result equals the sequential form bit for bit.
+constexpr int kQCap = 32 * (kUnroll + 1);  // entries left after a flush (< 32) plus one group's appends
+
+template <int D>
+struct WarpQueue {
+    int cell[kQCap];
+    float w[kQCap];
+    unsigned char owner[kQCap];
+    float col[3][32];
+    float beta[D][32];     // beta of each lane's ray (unscaled)
+    unsigned int own_mask[32];
+};
+
+template <int PREC, int D>
+__device__ __forceinline__ void march_tile_queued(const CacheView &c, const RenderConst &r, const FrameDesc &F,
+                                                  int px, int py, bool active, WarpQueue<D> &q) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    RaySetup<PREC, D> R;
+    if (active) {
+        R.init(c, r, F, px, py);
+    } else {
+        R.i_lo = R.i_hi = 0;
+        R.dcell = 0;
+        R.sigma_scale = 1.0f;
+    }
+    // unscaled beta of this lane's ray (FP8 folds the channel scales at shading)
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        float b = 0.0f;
+        if (active)
+            b = c.dir_prec == FNR_PREC_FP16
+                    ? __half2float(__ldg(static_cast<const __half *>(c.beta) + (long long)R.dcell * D + i))
+                    : __ldg(static_cast<const float *>(c.beta) + (long long)R.dcell * D + i);
+        q.beta[i][lane] = b;
+    }
+    float T = 1.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
+    long long S = 0;
+    int n_look = 0, n_occ = 0, n_steps = r.N;
+    const long long pix = active ? static_cast<long long>(py) * F.W + px : 0;
+    int32_t *cells_out = (active && F.cells) ? F.cells + pix * r.N : nullptr;
+    bool done = !active;
+    if (cells_out)
+        for (int i = 0; i < R.i_lo; ++i) cells_out[i] = -1;
+    const bool has_range = active && R.i_lo < R.i_hi;
+    const int lo_w = __reduce_min_sync(FULL, has_range ? R.i_lo : 0x7fffffff);
+    const int hi_w = __reduce_max_sync(FULL, has_range ? R.i_hi : 0);
+
+    // Shade queue entries [base, base + n) and add them to their owners.
+    auto flush = [&](int base, int n) {
+        float col[3] = {0.0f, 0.0f, 0.0f};
+        int own = 32 + lane;  // distinct dummy for lanes without an entry
+        if (lane < n) {
+            const int e = base + lane;
+            own = q.owner[e];
+            Record<PREC, D> rec;
+            rec.load(c.uvw + static_cast<long long>(q.cell[e]) * c.rec_stride);
+            float b[RaySetup<PREC, D>::NB];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const float bi = q.beta[i][own];
+                if constexpr (PREC == FNR_PREC_FP8_E4M3) {
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) b[ch * D + i] = bi * __ldg(c.scales + 1 + ch * D + i);
+                } else {
+                    b[i] = bi;
+                }
+            }
+            R.shade(rec, r.act, b, col);
+        }
+        q.col[0][lane] = col[0];
+        q.col[1][lane] = col[1];
+        q.col[2][lane] = col[2];
+        q.own_mask[lane] = 0u;
+        __syncwarp();
+        const unsigned m = __match_any_sync(FULL, own);
+        if (lane < n && lane == __ffs(m) - 1) q.own_mask[own] = m;
+        __syncwarp();
+        unsigned mine = q.own_mask[lane];
+        while (mine) {  // this lane's entries, in queue (= sample) order
+            const int j = __ffs(mine) - 1;
+            mine &= mine - 1;
+            const float w = q.w[base + j];
+            Cr = __fmaf_rn(w, q.col[0][j], Cr);
+            Cg = __fmaf_rn(w, q.col[1][j], Cg);
+            Cb = __fmaf_rn(w, q.col[2][j], Cb);
+        }
+        __syncwarp();
+    };
+
+    int qn = 0;
+    for (int i0 = lo_w; i0 < hi_w; i0 += kUnroll) {
+        if (!__any_sync(FULL, !done)) break;
+        // samples of this group the lane visits: [i_lo, i_hi) before termination
+        const int vlo = min(max(R.i_lo - i0, 0), kUnroll), vhi = min(max(R.i_hi - i0, 0), kUnroll);
+        const unsigned vis = done ? 0u : (((1u << vhi) - 1u) & ~((1u << vlo) - 1u));
+        int cell[kUnroll];
+        float sg[kUnroll];
+        float fi = __fadd_rn(static_cast<float>(i0), 0.5f);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            cell[u] = ((vis >> u) & 1u) ? R.cell_of(c, fi) : -1;
+            fi = __fadd_rn(fi, 1.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) sg[u] = cell[u] >= 0 ? load_sigma<PREC>(c, cell[u], R.sigma_scale) : 0.0f;
+        unsigned in_m = 0u, occ_m = 0u;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            in_m |= (cell[u] >= 0 ? 1u : 0u) << u;
+            occ_m |= (sg[u] > 0.0f ? 1u : 0u) << u;
+        }
+        if (cells_out) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if ((vis >> u) & 1u) cells_out[i0 + u] = cell[u];  // past termination: overwritten by -2 below
+        }
+        if (!__any_sync(FULL, occ_m != 0u)) {  // empty space for the whole warp
+            n_look += __popc(in_m);
+            continue;
+        }
+        // Occupied samples of this lane, in order: weights, transmittance, termination.
+        unsigned app = 0u, counted = in_m;
+        float aw[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            aw[u] = 0.0f;
+            if (((occ_m >> u) & 1u) && !done) {
+                float ext, alpha;
+                extinction(__fmul_rn(sg[u], r.dt), ext, alpha);
+                aw[u] = T * alpha;
+                T = T * ext;
+                app |= 1u << u;
+                const long long qd = fixed_depth(sg[u]);
+                S = (S > 0x7fffffffffffffffLL - qd) ? 0x7fffffffffffffffLL : S + qd;
+                if (S >= r.s_thr) {
+                    n_steps = i0 + u + 1;
+                    done = true;
+                    counted = in_m & ((2u << u) - 1u);
+                }
+            }
+        }
+        n_look += __popc(counted);
+        const int cnt = __popc(app);
+        n_occ += cnt;
+        // append lane by lane (per owner: sample order)
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += v;
+        }
+        int pos = qn + incl - cnt;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if ((app >> u) & 1u) {
+                q.cell[pos] = cell[u];
+                q.w[pos] = aw[u];
+                q.owner[pos] = static_cast<unsigned char>(lane);
+                ++pos;
+            }
+        }
+        qn += __shfl_sync(FULL, incl, 31);
+        if (qn >= 32) {
+            __syncwarp();
+            int base = 0;
+            for (; base + 32 <= qn; base += 32) flush(base, 32);
+            const int rem = qn - base;  // < 32, moved to the front (source >= 32 > target)
+            if (lane < rem) {
+                q.cell[lane] = q.cell[base + lane];
+                q.w[lane] = q.w[base + lane];
+                q.owner[lane] = q.owner[base + lane];
+            }
+            __syncwarp();
+            qn = rem;
+        }
+    }
+    if (qn > 0) {
+        __syncwarp();
+        flush(0, qn);
+    }
+    if (!active) return;
+    if (cells_out) {
+        if (done)
+            for (int i = n_steps; i < r.N; ++i) cells_out[i] = -2;
+        else
+            for (int i = max(R.i_hi, R.i_lo); i < r.N; ++i) cells_out[i] = -1;
+    }
+    float4 o;
+    o.x = __fmaf_rn(T, r.bg[0], Cr);
+    o.y = __fmaf_rn(T, r.bg[1], Cg);
+    o.z = __fmaf_rn(T, r.bg[2], Cb);
+    o.w = 1.0f - T;
+    reinterpret_cast<float4 *>(F.rgba)[pix] = o;
+    if (F.stats) reinterpret_cast<int4 *>(F.stats)[pix] = make_int4(n_steps, n_look, n_occ, R.dcell);
+}
+
+}  // namespace dev
+}  // namespace fnr

@@ -1,0 +1,574 @@
+// serve.cu -- continuous-batching request loop: fnr_submit / fnr_poll / fnr_wait.
+//
+// A scheduler thread admits queued requests into batch slots as slots and
+// HBM budget free up. Each slot launches one persistent kernel per batch on
+// its own stream (through a captured CUDA graph: table upload, scratch reset,
+// kernel). The kernel's warps pop 8 x 4 pixel tiles of all the batch's
+// requests from an atomic counter; the warp that finishes a request's last
+// tile writes the batch epoch into that request's host-mapped completion
+// word, so a request completes as soon as its own tiles are done, while the
+// rest of its batch -- and batches on the other slots -- keep the GPU busy.
+// No device code waits on anything: completion is observed by the host.
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "march_device.cuh"
+
+namespace fnr {
+
+fnr_status fail(fnr_status st, const char *fmt, ...);
+fnr_status cuda_fail(cudaError_t e, const char *what);
+void clear_error();
+fnr_status make_render_const(const fnr_render_params *p, RenderConst *rc);
+fnr_status check_camera(const fnr_camera *c);
+void fill_frame(FrameDesc *f, const fnr_camera *cam, float *rgba, fnr_ray_stats *stats, int32_t *cells,
+                int tile_begin);
+int frame_tiles(const fnr_camera *cam);
+bool cache_belongs(fnr_context *ctx, const fnr_cache *c);
+bool budget_charge(fnr_context *ctx, uint64_t bytes);
+void budget_uncharge(fnr_context *ctx, uint64_t bytes);
+
+constexpr int kMaxBatch = 64;
+constexpr int kMaxSlots = 8;
+
+struct ServeFrame {
+    CacheView c;
+    RenderConst r;
+    FrameDesc f;  // f.tile_begin: first batch tile of this request
+    int32_t n_tiles;
+    int32_t pad;
+};
+
+struct ServeTable {
+    int32_t n_frames;
+    int32_t total_tiles;
+    uint32_t epoch;
+    int32_t pad;
+    int32_t tile_begin[kMaxBatch + 1];
+    ServeFrame frames[kMaxBatch];
+};
+
+struct ServeScratch {  // zeroed before every launch
+    unsigned int next_tile;
+    unsigned int pad[31];
+    unsigned int done_tiles[kMaxBatch];
+};
+
+namespace {
+
+template <int PREC, int D>
+__global__ void __launch_bounds__(FNR_BLOCK, FNR_MINB)
+    serve_kernel(const ServeTable *__restrict__ tab, ServeScratch *scr, volatile uint32_t *done_flags) {
+    __shared__ dev::WarpQueue<D> queues[FNR_BLOCK / 32];
+    const int lane = threadIdx.x & 31;
+    const int total = tab->total_tiles;
+    const int nf = tab->n_frames;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = static_cast<int>(atomicAdd(&scr->next_tile, 1u));
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total) break;
+        int lo = 0, hi = nf - 1;  // last frame whose first tile is <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab->tile_begin[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const ServeFrame &sf = tab->frames[lo];
+        const int lt = t - tab->tile_begin[lo];
+        const int ty = lt / sf.f.tiles_x, tx = lt - ty * sf.f.tiles_x;
+        const int px = tx * kTileW + (lane & (kTileW - 1)), py = ty * kTileH + lane / kTileW;
+        dev::march_tile_queued<PREC, D>(sf.c, sf.r, sf.f, px, py, px < sf.f.W && py < sf.f.H,
+                                        queues[threadIdx.x >> 5]);
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(&scr->done_tiles[lo], 1u);
+            if (prev + 1u == static_cast<unsigned>(sf.n_tiles)) {
+                __threadfence_system();
+                done_flags[lo] = tab->epoch;
+            }
+        }
+    }
+}
+
+using ServeFn = void (*)(const ServeTable *, ServeScratch *, volatile uint32_t *);
+
+template <int PREC>
+ServeFn serve_fn_p(int D) {
+    switch (D) {
+        case 1: return serve_kernel<PREC, 1>;
+        case 2: return serve_kernel<PREC, 2>;
+        case 3: return serve_kernel<PREC, 3>;
+        case 4: return serve_kernel<PREC, 4>;
+        case 6: return serve_kernel<PREC, 6>;
+        case 8: return serve_kernel<PREC, 8>;
+        case 12: return serve_kernel<PREC, 12>;
+        case 16: return serve_kernel<PREC, 16>;
+        default: return nullptr;
+    }
+}
+
+ServeFn serve_fn(int prec, int D) {
+    switch (prec) {
+        case FNR_PREC_FP32: return serve_fn_p<FNR_PREC_FP32>(D);
+        case FNR_PREC_FP16: return serve_fn_p<FNR_PREC_FP16>(D);
+        case FNR_PREC_FP8_E4M3: return serve_fn_p<FNR_PREC_FP8_E4M3>(D);
+        default: return nullptr;
+    }
+}
+
+uint64_t now_ns() {
+    return static_cast<uint64_t>(
+        std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+            .count());
+}
+
+struct Request {
+    fnr_request req;
+    RenderConst rc;
+    uint64_t bytes = 0;  // charged against the budget while admitted
+    int key = 0;         // prec * 32 + D: one kernel instance per batch
+    int64_t rays = 0;
+    int32_t tiles = 0;
+    uint64_t t_submit = 0, t_admit = 0, t_done = 0;
+    fnr_status status = FNR_ERR_NOT_READY;
+    bool queued = true;
+    int64_t batch = -1;
+    cudaEvent_t ready = nullptr;  // recorded on the request's stream at submit
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    ServeTable *h_table = nullptr;  // pinned
+    ServeTable *d_table = nullptr;
+    ServeScratch *d_scratch = nullptr;
+    uint32_t *h_flags = nullptr;  // pinned, mapped
+    uint32_t *d_flags = nullptr;
+    uint32_t epoch = 0;
+    bool busy = false;
+    int n = 0;
+    uint64_t tickets[kMaxBatch];
+    bool done[kMaxBatch];
+    int remaining = 0;
+    std::map<int, cudaGraphExec_t> graphs;
+};
+
+}  // namespace
+
+struct Server {
+    fnr_context *ctx = nullptr;
+    fnr_serve_config cfg;
+    std::mutex mu;
+    std::condition_variable cv_sched, cv_done;
+    std::deque<uint64_t> pending;
+    std::unordered_map<uint64_t, Request> reqs;
+    std::vector<Slot> slots;
+    std::thread th;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    int64_t next_batch = 0;
+    std::map<int, int> grid_blocks;  // key -> persistent grid size
+    fnr_status fatal = FNR_OK;
+
+    int grid_for(int key, ServeFn fn) {
+        auto it = grid_blocks.find(key);
+        if (it != grid_blocks.end()) return it->second;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(fn), FNR_BLOCK, 0);
+        const int g = std::max(1, per_sm) * std::max(1, ctx->num_sms);
+        grid_blocks[key] = g;
+        return g;
+    }
+
+    void complete(Request &r, fnr_status st) {
+        r.status = st;
+        r.t_done = now_ns();
+        budget_uncharge(ctx, r.bytes);
+        r.bytes = 0;
+        const_cast<fnr_cache *>(r.req.cache)->inflight.fetch_sub(1);
+    }
+
+    // Completion words of busy slots -> finished requests; frees slots.
+    bool poll_locked() {
+        bool progress = false;
+        for (Slot &s : slots) {
+            if (!s.busy) continue;
+            for (int f = 0; f < s.n; ++f) {
+                if (s.done[f]) continue;
+                if (reinterpret_cast<volatile uint32_t *>(s.h_flags)[f] == s.epoch) {
+                    std::atomic_thread_fence(std::memory_order_acquire);
+                    auto it = reqs.find(s.tickets[f]);
+                    if (it != reqs.end()) complete(it->second, FNR_OK);
+                    s.done[f] = true;
+                    --s.remaining;
+                    progress = true;
+                }
+            }
+            const cudaError_t q = cudaEventQuery(s.done_ev);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess || s.remaining > 0) {
+                // the launch failed, or ended without flagging some request
+                const fnr_status st = q != cudaSuccess ? FNR_ERR_CUDA : FNR_ERR_DEVICE;
+                for (int f = 0; f < s.n; ++f)
+                    if (!s.done[f]) {
+                        if (reinterpret_cast<volatile uint32_t *>(s.h_flags)[f] == s.epoch && q == cudaSuccess) {
+                            auto it = reqs.find(s.tickets[f]);
+                            if (it != reqs.end()) complete(it->second, FNR_OK);
+                        } else {
+                            auto it = reqs.find(s.tickets[f]);
+                            if (it != reqs.end()) complete(it->second, st);
+                        }
+                        s.done[f] = true;
+                    }
+                s.remaining = 0;
+                if (q != cudaSuccess) fatal = FNR_ERR_CUDA;
+            }
+            s.busy = false;
+            progress = true;
+        }
+        if (progress) cv_done.notify_all();
+        return progress;
+    }
+
+    fnr_status launch(Slot &s, int key) {
+        ServeFn fn = serve_fn(key / 32, key % 32);
+        const int grid = grid_for(key, fn);
+        cudaError_t e;
+        if (cfg.use_graphs) {
+            auto it = s.graphs.find(key);
+            if (it == s.graphs.end()) {
+                cudaGraph_t g = nullptr;
+                cudaGraphExec_t ge = nullptr;
+                if ((e = cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                    return cuda_fail(e, "graph capture");
+                cudaMemcpyAsync(s.d_table, s.h_table, sizeof(ServeTable), cudaMemcpyHostToDevice, s.stream);
+                cudaMemsetAsync(s.d_scratch, 0, sizeof(ServeScratch), s.stream);
+                fn<<<grid, FNR_BLOCK, 0, s.stream>>>(s.d_table, s.d_scratch, s.d_flags);
+                if ((e = cudaStreamEndCapture(s.stream, &g)) != cudaSuccess) return cuda_fail(e, "graph capture");
+                e = cudaGraphInstantiate(&ge, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+                it = s.graphs.emplace(key, ge).first;
+            }
+            if ((e = cudaGraphLaunch(it->second, s.stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+        } else {
+            if ((e = cudaMemcpyAsync(s.d_table, s.h_table, sizeof(ServeTable), cudaMemcpyHostToDevice, s.stream)) !=
+                    cudaSuccess ||
+                (e = cudaMemsetAsync(s.d_scratch, 0, sizeof(ServeScratch), s.stream)) != cudaSuccess)
+                return cuda_fail(e, "batch upload");
+            fn<<<grid, FNR_BLOCK, 0, s.stream>>>(s.d_table, s.d_scratch, s.d_flags);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "serve launch");
+        }
+        if ((e = cudaEventRecord(s.done_ev, s.stream)) != cudaSuccess) return cuda_fail(e, "event record");
+        return FNR_OK;
+    }
+
+    // Queued requests -> free slots, in arrival order, one kernel key per batch.
+    bool admit_locked() {
+        bool progress = false;
+        for (Slot &s : slots) {
+            if (s.busy || pending.empty()) continue;
+            ServeTable &tb = *s.h_table;
+            int n = 0, tiles = 0, key = -1;
+            int64_t rays = 0;
+            bool blocked = false;
+            for (auto it = pending.begin(); it != pending.end() && n < cfg.max_batch_requests;) {
+                Request &r = reqs[*it];
+                if (key < 0) key = r.key;
+                if (r.key != key) {
+                    ++it;
+                    continue;
+                }
+                if (n > 0 && rays + r.rays > cfg.max_batch_rays) break;
+                if (!budget_charge(ctx, r.bytes)) {  // wait for memory to free up
+                    blocked = true;
+                    break;
+                }
+                ServeFrame &sf = tb.frames[n];
+                sf.c = r.req.cache->view;
+                sf.r = r.rc;
+                fill_frame(&sf.f, &r.req.camera, r.req.rgba_dev, r.req.stats_dev, nullptr, tiles);
+                sf.n_tiles = r.tiles;
+                tb.tile_begin[n] = tiles;
+                tiles += r.tiles;
+                rays += r.rays;
+                r.queued = false;
+                r.t_admit = now_ns();
+                r.batch = next_batch;
+                s.tickets[n] = *it;
+                s.done[n] = false;
+                ++n;
+                it = pending.erase(it);
+            }
+            if (n == 0) {
+                if (blocked) break;
+                continue;
+            }
+            tb.n_frames = n;
+            tb.total_tiles = tiles;
+            tb.tile_begin[n] = tiles;
+            tb.epoch = ++s.epoch;
+            for (int f = 0; f < n; ++f) {  // outputs prepared on the callers' streams come first
+                Request &r = reqs[s.tickets[f]];
+                if (r.ready) {
+                    cudaStreamWaitEvent(s.stream, r.ready, 0);
+                    cudaEventDestroy(r.ready);
+                    r.ready = nullptr;
+                }
+            }
+            s.n = n;
+            s.remaining = n;
+            s.busy = true;
+            ++next_batch;
+            const fnr_status st = launch(s, key);
+            if (st != FNR_OK) {
+                for (int f = 0; f < n; ++f) {
+                    auto it = reqs.find(s.tickets[f]);
+                    if (it != reqs.end()) complete(it->second, st);
+                }
+                s.busy = false;
+                fatal = st;
+                cv_done.notify_all();
+            }
+            progress = true;
+            if (blocked) break;
+        }
+        return progress;
+    }
+
+    void loop() {
+        cudaSetDevice(ctx->device);
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            bool busy = false;
+            for (Slot &s : slots) busy |= s.busy;
+            if (stop && pending.empty() && !busy) break;
+            const bool p1 = poll_locked();
+            const bool p2 = admit_locked();
+            busy = false;
+            for (Slot &s : slots) busy |= s.busy;
+            if (p1 || p2) continue;
+            if (busy) {
+                lk.unlock();
+                std::this_thread::yield();  // completion words are polled, not waited on
+                lk.lock();
+            } else {
+                cv_sched.wait_for(lk, std::chrono::milliseconds(5));
+            }
+        }
+    }
+};
+
+static fnr_status server_start(fnr_context *ctx, const fnr_serve_config *cfg_in) {
+    fnr_serve_config cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    if (cfg_in) cfg = *cfg_in;
+    if (cfg.queue_capacity <= 0) cfg.queue_capacity = 4096;
+    if (cfg.max_batch_requests <= 0) cfg.max_batch_requests = kMaxBatch;
+    if (cfg.max_batch_requests > kMaxBatch)
+        return fail(FNR_ERR_INVALID_ARG, "max_batch_requests > %d", kMaxBatch);
+    if (cfg.max_batch_rays <= 0) cfg.max_batch_rays = int64_t(16) << 20;
+    if (cfg.n_slots <= 0) cfg.n_slots = 3;
+    if (cfg.n_slots > kMaxSlots) return fail(FNR_ERR_INVALID_ARG, "n_slots > %d", kMaxSlots);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    Server *sv = new Server();
+    sv->ctx = ctx;
+    sv->cfg = cfg;
+    sv->slots.resize(cfg.n_slots);
+    fnr_status st = FNR_OK;
+    for (Slot &s : sv->slots) {
+        if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&s.done_ev, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaHostAlloc(reinterpret_cast<void **>(&s.h_table), sizeof(ServeTable), cudaHostAllocDefault)) !=
+                cudaSuccess ||
+            (e = cudaMalloc(&s.d_table, sizeof(ServeTable))) != cudaSuccess ||
+            (e = cudaMalloc(&s.d_scratch, sizeof(ServeScratch))) != cudaSuccess ||
+            (e = cudaHostAlloc(reinterpret_cast<void **>(&s.h_flags), sizeof(uint32_t) * kMaxBatch,
+                               cudaHostAllocMapped)) != cudaSuccess ||
+            (e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s.d_flags), s.h_flags, 0)) != cudaSuccess) {
+            st = cuda_fail(e, "serving slot setup");
+            break;
+        }
+        memset(s.h_table, 0, sizeof(ServeTable));
+        memset(s.h_flags, 0, sizeof(uint32_t) * kMaxBatch);
+    }
+    if (st != FNR_OK) {
+        for (Slot &s : sv->slots) {
+            if (s.stream) cudaStreamDestroy(s.stream);
+            if (s.done_ev) cudaEventDestroy(s.done_ev);
+            if (s.h_table) cudaFreeHost(s.h_table);
+            if (s.d_table) cudaFree(s.d_table);
+            if (s.d_scratch) cudaFree(s.d_scratch);
+            if (s.h_flags) cudaFreeHost(s.h_flags);
+        }
+        delete sv;
+        return st;
+    }
+    sv->th = std::thread([sv] { sv->loop(); });
+    ctx->server = sv;
+    return FNR_OK;
+}
+
+void server_stop(fnr_context *ctx) {
+    Server *sv = ctx->server;
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> g(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_sched.notify_all();
+    sv->th.join();
+    cudaSetDevice(ctx->device);
+    for (Slot &s : sv->slots) {
+        cudaStreamSynchronize(s.stream);
+        for (auto &kv : s.graphs) cudaGraphExecDestroy(kv.second);
+        cudaStreamDestroy(s.stream);
+        cudaEventDestroy(s.done_ev);
+        cudaFreeHost(s.h_table);
+        cudaFree(s.d_table);
+        cudaFree(s.d_scratch);
+        cudaFreeHost(s.h_flags);
+    }
+    for (auto &kv : sv->reqs) {
+        if (kv.second.status == FNR_ERR_NOT_READY) const_cast<fnr_cache *>(kv.second.req.cache)->inflight.fetch_sub(1);
+        if (kv.second.ready) cudaEventDestroy(kv.second.ready);
+    }
+    delete sv;
+    ctx->server = nullptr;
+}
+
+static void fill_result(const Request &r, uint64_t ticket, fnr_result *out) {
+    if (!out) return;
+    out->status = r.status;
+    out->reserved = 0;
+    out->t_submit_ns = r.t_submit;
+    out->t_admit_ns = r.t_admit;
+    out->t_done_ns = r.t_done;
+    out->n_rays = static_cast<uint64_t>(r.rays);
+    out->batch = r.batch;
+    out->ticket = ticket;
+}
+
+}  // namespace fnr
+
+using namespace fnr;
+
+extern "C" {
+
+fnr_status fnr_serve_start(fnr_context *ctx, const fnr_serve_config *cfg) {
+    clear_error();
+    if (!ctx) return fail(FNR_ERR_INVALID_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> g(ctx->serve_mu);
+    if (ctx->server) return fail(FNR_ERR_INVALID_ARG, "the request loop is already running");
+    return server_start(ctx, cfg);
+}
+
+fnr_status fnr_serve_stop(fnr_context *ctx) {
+    clear_error();
+    if (!ctx) return fail(FNR_ERR_INVALID_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> g(ctx->serve_mu);
+    server_stop(ctx);
+    return FNR_OK;
+}
+
+fnr_status fnr_submit(fnr_context *ctx, const fnr_request *req, uint64_t *ticket) {
+    clear_error();
+    if (!ctx || !req || !ticket) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
+    *ticket = 0;
+    if (!req->cache || !req->rgba_dev) return fail(FNR_ERR_INVALID_ARG, "request needs a cache and an output");
+    if (!cache_belongs(ctx, req->cache)) return fail(FNR_ERR_INVALID_ARG, "cache does not belong to this context");
+    Request r;
+    r.req = *req;
+    fnr_status st = make_render_const(&req->params, &r.rc);
+    if (st != FNR_OK) return st;
+    if ((st = check_camera(&req->camera)) != FNR_OK) return st;
+    const int D = req->cache->desc.D;
+    if (!serve_fn(req->cache->desc.pos_precision, D))
+        return fail(FNR_ERR_UNSUPPORTED, "served rendering supports D in {1,2,3,4,6,8,12,16}, got %d", D);
+    r.key = req->cache->desc.pos_precision * 32 + D;
+    r.rays = int64_t(req->camera.width) * req->camera.height;
+    r.tiles = frame_tiles(&req->camera);
+    r.bytes = uint64_t(r.rays) * (16u + (req->stats_dev ? 16u : 0u));
+    {
+        std::lock_guard<std::mutex> g(ctx->serve_mu);
+        if (!ctx->server && (st = server_start(ctx, nullptr)) != FNR_OK) return st;
+    }
+    Server *sv = ctx->server;
+    if (ctx->budget && r.bytes > ctx->budget)
+        return fail(FNR_ERR_BUDGET, "request output (%llu bytes) exceeds the HBM budget",
+                    (unsigned long long)r.bytes);
+    {
+        std::lock_guard<std::mutex> g(sv->mu);
+        if (sv->fatal != FNR_OK) return fail(sv->fatal, "the request loop stopped after a device error");
+        if (static_cast<int>(sv->pending.size()) >= sv->cfg.queue_capacity)
+            return fail(FNR_ERR_QUEUE_FULL, "request queue is full (%d)", sv->cfg.queue_capacity);
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+        if ((e = cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "request event");
+        if ((e = cudaEventRecord(r.ready, reinterpret_cast<cudaStream_t>(req->stream))) != cudaSuccess) {
+            cudaEventDestroy(r.ready);
+            return cuda_fail(e, "request event record");
+        }
+        r.t_submit = now_ns();
+        const uint64_t t = sv->next_ticket++;
+        const_cast<fnr_cache *>(req->cache)->inflight.fetch_add(1);
+        sv->reqs.emplace(t, r);
+        sv->pending.push_back(t);
+        *ticket = t;
+    }
+    sv->cv_sched.notify_one();
+    return FNR_OK;
+}
+
+fnr_status fnr_poll(fnr_context *ctx, uint64_t ticket, fnr_result *out) {
+    clear_error();
+    if (!ctx || !ctx->server) return fail(FNR_ERR_INVALID_ARG, "no request loop");
+    Server *sv = ctx->server;
+    std::lock_guard<std::mutex> g(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return fail(FNR_ERR_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    if (it->second.status == FNR_ERR_NOT_READY) sv->poll_locked();
+    if (it->second.status == FNR_ERR_NOT_READY) {
+        fill_result(it->second, ticket, out);
+        return FNR_ERR_NOT_READY;
+    }
+    fill_result(it->second, ticket, out);
+    sv->reqs.erase(it);
+    return FNR_OK;
+}
+
+fnr_status fnr_wait(fnr_context *ctx, uint64_t ticket, uint32_t timeout_ms, fnr_result *out) {
+    clear_error();
+    if (!ctx || !ctx->server) return fail(FNR_ERR_INVALID_ARG, "no request loop");
+    Server *sv = ctx->server;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return fail(FNR_ERR_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    while (it->second.status == FNR_ERR_NOT_READY) {
+        if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+            it = sv->reqs.find(ticket);
+            if (it->second.status != FNR_ERR_NOT_READY) break;
+            fill_result(it->second, ticket, out);
+            return fail(FNR_ERR_TIMEOUT, "request %llu not done after %u ms", (unsigned long long)ticket,
+                        timeout_ms);
+        }
+        it = sv->reqs.find(ticket);
+    }
+    fill_result(it->second, ticket, out);
+    sv->reqs.erase(it);
+    return FNR_OK;
+}
+
+}  // extern "C"
