@@ -293,6 +293,31 @@ FNR_API fnr_status fnr_poll(fnr_context *ctx, uint64_t ticket, fnr_result *out);
 /* As fnr_poll, blocking up to timeout_ms; FNR_ERR_TIMEOUT if still not done. */
 FNR_API fnr_status fnr_wait(fnr_context *ctx, uint64_t ticket, uint32_t timeout_ms, fnr_result *out);
 
+/* ------------------------------------------------------------------ rendering without allocation */
+/* The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory: a process whose HBM is owned by another allocator
+ * that has already reserved nearly all of it, a render loop that must never
+ * stall on cudaMalloc / cudaFree (cudaFree synchronises the device), or a host
+ * that plans every byte of device memory up front.
+ *
+ * Renders up to 32 views of one cache, like fnr_render, with the persistent
+ * tile-popping kernel of the request loop, and allocates nothing: the kernel's
+ * scratch (a tile counter and one finished-tile counter per view) is a 256-byte
+ * static __device__ array that every GPU loading the library holds until the
+ * process exits. Views, caches and outputs are the caller's, laid out as for
+ * fnr_render; done_words (nullable; device-visible, e.g. host-mapped) gets 1
+ * in word f when view f is finished. Stream-ordered on `stream`.
+ * The first call on a device looks up the array's device address (with that
+ * device current), so make that first call before any stream capture. Every
+ * call shares the array and clears the counters it uses before its launch:
+ * calls whose launches overlap on the GPU race, so keep them on one stream or
+ * order them. Errors: INVALID_ARG (more than 32 views: the scratch holds one
+ * counter per view; NULL arguments; bad params), UNSUPPORTED (D not in
+ * {1,2,3,4,6,8,12,16}), CUDA. */
+FNR_API fnr_status fnr_render_noalloc(const fnr_cache *cache, const fnr_camera *cams, int32_t n_cams,
+                                      const fnr_render_params *params, float *rgba_dev, fnr_ray_stats *stats_dev,
+                                      uint32_t *done_words, fnr_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -122,6 +122,8 @@ SIGNATURES = {
     "fnr_submit": ([_P, ctypes.POINTER(fnr_request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int32),
     "fnr_poll": ([_P, ctypes.c_uint64, ctypes.POINTER(fnr_result)], ctypes.c_int32),
     "fnr_wait": ([_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(fnr_result)], ctypes.c_int32),
+    "fnr_render_noalloc": ([_P, ctypes.POINTER(fnr_camera), ctypes.c_int32, ctypes.POINTER(fnr_render_params), _P,
+                            _P, _P, _P], ctypes.c_int32),
 }
 
 _lib = None
@@ -295,3 +297,19 @@ def fnr_wait(ctx: int, ticket: int, timeout_ms: int = 10000) -> fnr_result:
     out = fnr_result()
     check(lib().fnr_wait(ctx, ticket, timeout_ms, ctypes.byref(out)))
     return out
+
+
+# ------------------------------------------------------------------ rendering without allocation
+def fnr_render_noalloc(cache: int, cams, params: fnr_render_params, rgba, stats=None, done_words=None,
+                       stream=None):
+    """Render up to 32 views with the persistent kernel whose scratch is a static device array (for callers
+    that cannot allocate device memory). Same output layout as fnr_render."""
+    cams = [c if isinstance(c, fnr_camera) else make_camera(c) for c in cams]
+    arr = (fnr_camera * len(cams))(*cams)
+    npix = sum(c.width * c.height for c in cams)
+    assert rgba.is_cuda and rgba.is_contiguous() and rgba.numel() >= 4 * npix
+    if stats is not None:
+        assert stats.is_cuda and stats.is_contiguous() and stats.numel() >= 4 * npix
+    check(lib().fnr_render_noalloc(cache, arr, len(cams), ctypes.byref(params), rgba.data_ptr(),
+                                   None if stats is None else stats.data_ptr(),
+                                   None if done_words is None else done_words.data_ptr(), _stream_handle(stream)))
