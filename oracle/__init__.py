@@ -322,3 +322,27 @@ def mlp_forward(weights, biases, x: np.ndarray, round_bf16: bool, nthreads=None)
     if rc != 0:
         raise ValueError("orc_mlp_forward rejected its arguments")
     return out
+
+
+# ------------------------------------------------------------------ cache build from the MLPs (Section 3.3)
+def cell_centres(k: int, cells, bmin=(-1.5, -1.5, -1.5), bmax=(1.5, 1.5, 1.5)) -> np.ndarray:
+    """FP64 grid sample of linear cell index (z*k + y)*k + x: bmin + (j + 1/2)(bmax - bmin)/k per axis."""
+    cells = np.asarray(cells, dtype=np.int64)
+    idx = np.stack([cells % k, (cells // k) % k, cells // (k * k)], axis=1).astype(np.float64)
+    lo, hi = np.asarray(bmin, np.float64), np.asarray(bmax, np.float64)
+    return lo + (idx + 0.5) * ((hi - lo) / k)
+
+
+def bin_directions(l: int, bins) -> np.ndarray:
+    """FP64 unit direction of bin i_theta*l + i_phi: theta = (i_theta + 1/2) pi / l from +z,
+    phi = (i_phi + 1/2) 2 pi / l."""
+    bins = np.asarray(bins, dtype=np.int64)
+    th = (bins // l + 0.5) * (np.pi / l)
+    ph = (bins % l + 0.5) * (2.0 * np.pi / l)
+    return np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
+
+
+def mlp_eval(layers, x: np.ndarray, L: int, round_bf16: bool, nthreads=None) -> np.ndarray:
+    """F(x): positional encoding with L frequencies, then the MLP (layers: [(W FP64 [out][in], b FP64)])."""
+    enc = posenc(x, L, layers[0][0].shape[1])
+    return mlp_forward([W for W, _ in layers], [b for _, b in layers], enc, round_bf16, nthreads)

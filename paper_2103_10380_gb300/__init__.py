@@ -211,6 +211,37 @@ def fnr_build_cache(ctx: int, desc: fnr_cache_desc, sigma, uvw, beta, stream=Non
     return out.value
 
 
+def make_mlp(layers, pe_freqs: int) -> fnr_mlp:
+    """layers: [(W, b)] with W a CUDA tensor of bf16 bits [out][in] (int16/uint16/bfloat16), b float32 [out]."""
+    m = fnr_mlp()
+    m.n_layers = len(layers)
+    m.pe_in = 3
+    m.pe_freqs = pe_freqs
+    dims = [int(layers[0][0].shape[1])] + [int(W.shape[0]) for W, _ in layers]
+    for i, d in enumerate(dims):
+        m.dims[i] = d
+    for i, (W, b) in enumerate(layers):
+        assert W.is_cuda and W.is_contiguous() and W.element_size() == 2
+        assert b.is_cuda and b.is_contiguous() and str(b.dtype) == "torch.float32"
+        m.weights[i] = W.data_ptr()
+        m.biases[i] = b.data_ptr()
+    return m
+
+
+def fnr_build_cache_mlp(ctx: int, desc: fnr_cache_desc, pos_layers, dir_layers, pos_freqs: int = 10,
+                        dir_freqs: int = 4, stream=None) -> int:
+    """Build a cache by evaluating F_pos over the k^3 cell centres and F_dir over the l x l bin centres."""
+    pm, dm = make_mlp(pos_layers, pos_freqs), make_mlp(dir_layers, dir_freqs)
+    src = fnr_cache_source()
+    src.kind = FNR_SRC_MLP
+    src.pos_mlp = ctypes.addressof(pm)
+    src.dir_mlp = ctypes.addressof(dm)
+    out = _P()
+    check(lib().fnr_build_cache(ctx, ctypes.byref(desc), ctypes.byref(src), _stream_handle(stream),
+                                ctypes.byref(out)))
+    return out.value
+
+
 def fnr_cache_free(ctx: int, cache: int):
     check(lib().fnr_cache_free(ctx, cache))
 

@@ -348,11 +348,19 @@ fnr_status fnr_build_cache(fnr_context *ctx, const fnr_cache_desc *desc, const f
     if (!ctx || !desc || !src || !out) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     if (!desc_valid(desc)) return fail(FNR_ERR_INVALID_ARG, "invalid cache descriptor");
-    if (src->kind == FNR_SRC_MLP) return fail(FNR_ERR_UNSUPPORTED, "MLP source not available in this build");
-    if (src->kind != FNR_SRC_ARRAYS) return fail(FNR_ERR_INVALID_ARG, "unknown source kind %d", src->kind);
-    if (!src->sigma || !src->uvw || !src->beta) return fail(FNR_ERR_INVALID_ARG, "NULL source array");
-    if (src->location != FNR_LOC_HOST && src->location != FNR_LOC_DEVICE)
-        return fail(FNR_ERR_INVALID_ARG, "unknown source location");
+    fnr_status st0;
+    if (src->kind == FNR_SRC_MLP) {
+        if ((st0 = check_mlp(src->pos_mlp, 1 + 3 * desc->D, "pos_mlp")) != FNR_OK) return st0;
+        if ((st0 = check_mlp(src->dir_mlp, desc->D, "dir_mlp")) != FNR_OK) return st0;
+        if (desc->pos_precision == FNR_PREC_FP8_E4M3)
+            return fail(FNR_ERR_UNSUPPORTED, "MLP builds write FP32 or FP16 caches (build FP8 from arrays)");
+    } else if (src->kind == FNR_SRC_ARRAYS) {
+        if (!src->sigma || !src->uvw || !src->beta) return fail(FNR_ERR_INVALID_ARG, "NULL source array");
+        if (src->location != FNR_LOC_HOST && src->location != FNR_LOC_DEVICE)
+            return fail(FNR_ERR_INVALID_ARG, "unknown source location");
+    } else {
+        return fail(FNR_ERR_INVALID_ARG, "unknown source kind %d", src->kind);
+    }
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     const Layout L = layout_of(desc);
@@ -385,7 +393,15 @@ fnr_status fnr_build_cache(fnr_context *ctx, const fnr_cache_desc *desc, const f
             st = cuda_fail(e, "scale upload");
         if (st == FNR_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "sync");
     }
-    if (st == FNR_OK) st = build_from_arrays(c, src, L, s);
+    if (st == FNR_OK) {
+        if (src->kind == FNR_SRC_ARRAYS) {
+            st = build_from_arrays(c, src, L, s);
+        } else {
+            fill_view(c, L);
+            st = run_mlp(src->pos_mlp, 0, c->desc, c->view, ctx->num_sms, s);
+            if (st == FNR_OK) st = run_mlp(src->dir_mlp, 1, c->desc, c->view, ctx->num_sms, s);
+        }
+    }
     if (st != FNR_OK) {
         cudaFree(c->base);
         budget_uncharge(ctx, L.total);

@@ -81,6 +81,11 @@ cudaError_t launch_scales_from_absmax(const unsigned *amax_bits, float *scales, 
 struct Server;
 void server_stop(fnr_context *ctx);
 
+// mlp.cu: tensor-core evaluation of F_pos (mode 0) / F_dir (mode 1) into a cache.
+fnr_status check_mlp(const fnr_mlp *m, int n_out_min, const char *name);
+fnr_status run_mlp(const fnr_mlp *m, int mode, const fnr_cache_desc &d, const CacheView &v, int num_sms,
+                   cudaStream_t s);
+
 }  // namespace fnr
 
 struct fnr_cache {

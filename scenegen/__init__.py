@@ -332,3 +332,35 @@ def scale(seed: int = 0, k: int = 512, l: int = 512, W: int = 800, H: int = 800,
     sc = make_scene(seed, n_spheres=32, n_shells=16, D=8, sh_degree=4)
     return Workload(f"scale-k{k}-D8-{W}x{H}-N{n_samples}", sc, k=k, l=l, D=8, W=W, H=H, n_samples=n_samples,
                     n_cams=n_cams, cam_seed=seed + 1, hemisphere=True)
+
+
+# ---------------------------------------------------------------- MLP weights (cache-build inputs)
+def bf16_bits(x: np.ndarray) -> np.ndarray:
+    """binary32 -> bf16 bit patterns, round to nearest even (finite inputs)."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
+
+
+def bf16_value(bits: np.ndarray) -> np.ndarray:
+    return (bits.astype(np.uint32) << 16).view(np.float32)
+
+
+def mlp_weights(seed: int, dims: list, bias_scale: float = 0.0) -> list:
+    """He-uniform MLP weights W_i ~ U(-sqrt(6/fan_in), +sqrt(6/fan_in)), [out][in], stored as bf16 bits;
+    biases U(-bias_scale, bias_scale) as float32 (0 by default). Draws: numpy PCG64(seed), layer by layer,
+    weights then biases."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(len(dims) - 1):
+        fan_in, fan_out = dims[i], dims[i + 1]
+        lim = np.sqrt(6.0 / fan_in)
+        W = rng.uniform(-lim, lim, size=(fan_out, fan_in)).astype(np.float32)
+        b = rng.uniform(-bias_scale, bias_scale, size=fan_out).astype(np.float32) if bias_scale else \
+            np.zeros(fan_out, np.float32)
+        out.append((bf16_bits(W), b))
+    return out
+
+
+FPOS_DIMS_D8 = [60, 256, 256, 256, 256, 256, 256, 256, 256, 25]   # 8 ReLU layers of 256 + linear head
+FDIR_DIMS_D8 = [24, 128, 128, 128, 128, 8]                          # 4 ReLU layers of 128 + linear head

@@ -1,0 +1,176 @@
+"""Cache build from the F_pos / F_dir MLPs on the tensor cores, through the C ABI.
+
+Checked against the FP64 oracle's MLP evaluated at the same grid samples:
+(i) with the same bf16 weights and bf16 rounding of the network input and of
+every hidden activation (as the tensor-core chain stores them): per output
+channel relative L2 error <= 5e-3 and max |error| <= 8e-2 * rms(channel). The
+chain rounds fp32 accumulators to bf16 where the oracle rounds FP64 ones, so an
+activation near a bf16 rounding boundary can land one bf16 ulp (2^-8) apart and
+carry that through the later layers: rare, hence the max bound well above the
+L2 one (first measured run: max 3.8e-2 * rms). (ii) against pure FP64
+activations: relative L2 <= 5e-2. A single linear layer (no hidden rounding) is
+checked tightly (FP32 accumulation only), which pins the operand layouts."""
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fnr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2103_10380_gb300 as fnr
+    torch.cuda.set_device(0)
+    return fnr
+
+
+def device_bytes(ptr, nbytes):
+    import torch
+
+    class _V:
+        __cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False), "version": 3}
+
+    return torch.as_tensor(_V(), device="cuda").cpu().numpy()
+
+
+def to_device(layers):
+    import torch
+    return [(torch.from_numpy(W.view(np.int16)).cuda(), torch.from_numpy(b).cuda()) for W, b in layers]
+
+
+def as_fp64(layers):
+    return [(scenegen.bf16_value(W).astype(np.float64), b.astype(np.float64)) for W, b in layers]
+
+
+def read_cache(fnr, cache, k, D, l, prec=0, dprec=0):
+    lay = fnr.fnr_cache_get_layout(cache)
+    k3 = k ** 3
+    es = 4 if prec == 0 else 2
+    sdt = np.float32 if prec == 0 else np.float16
+    sig = device_bytes(lay.sigma_dev, k3 * es).view(sdt).astype(np.float64)
+    rec = device_bytes(lay.uvw_dev, k3 * lay.record_stride).reshape(k3, lay.record_stride)
+    uvw = np.ascontiguousarray(rec[:, :3 * D * es]).view(sdt).astype(np.float64).reshape(k3, 3 * D)
+    bes = 4 if dprec == 0 else 2
+    bdt = np.float32 if dprec == 0 else np.float16
+    beta = device_bytes(lay.beta_dev, l * l * D * bes).view(bdt).astype(np.float64).reshape(l * l, D)
+    return sig, uvw, beta
+
+
+def build(fnr, ctx, k, l, D, pos, dirn, prec=0, dprec=0):
+    desc = fnr.make_desc(k, D, l, prec, dprec)
+    return fnr.fnr_build_cache_mlp(ctx, desc, to_device(pos), to_device(dirn))
+
+
+def check_channels(got, ref, l2_rel=5e-3, max_rel=8e-2):
+    rms = np.sqrt(np.mean(ref ** 2, axis=0)) + 1e-12
+    l2 = np.sqrt(np.mean((got - ref) ** 2, axis=0)) / rms
+    mx = np.max(np.abs(got - ref), axis=0) / rms
+    print(f"per-channel relative L2 max {l2.max():.2e}, max |err|/rms {mx.max():.2e}")
+    assert np.all(l2 <= l2_rel), l2.max()
+    assert np.all(mx <= max_rel), mx.max()
+
+
+def test_single_linear_layer(fnr):
+    """One linear layer per MLP: only FP32 accumulation separates GPU and FP64."""
+    k, l, D = 8, 8, 8
+    pos = scenegen.mlp_weights(1, [60, 25], bias_scale=0.5)
+    dirn = scenegen.mlp_weights(2, [24, 8], bias_scale=0.5)
+    ctx = fnr.fnr_context_create(0, 0)
+    try:
+        cache = build(fnr, ctx, k, l, D, pos, dirn)
+        sig, uvw, beta = read_cache(fnr, cache, k, D, l)
+        xyz = oracle.cell_centres(k, np.arange(k ** 3))
+        out = oracle.mlp_eval(as_fp64(pos), xyz, 10, True)
+        np.testing.assert_allclose(sig, np.maximum(out[:, 0], 0), atol=2e-4)
+        np.testing.assert_allclose(uvw, out[:, 1:], atol=2e-4)
+        dirs = oracle.bin_directions(l, np.arange(l * l))
+        bout = oracle.mlp_eval(as_fp64(dirn), dirs, 4, True)
+        np.testing.assert_allclose(beta, bout, atol=2e-4)
+    finally:
+        fnr.fnr_context_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_architecture_small_grid(fnr, prec):
+    """8 x 256 ReLU F_pos (+ head) and 4 x 128 ReLU F_dir (+ head), k=16, l=16 (ragged last tile of F_dir)."""
+    k, l, D = 16, 12, 8
+    pos = scenegen.mlp_weights(3, scenegen.FPOS_DIMS_D8, bias_scale=0.05)
+    dirn = scenegen.mlp_weights(4, scenegen.FDIR_DIMS_D8, bias_scale=0.05)
+    ctx = fnr.fnr_context_create(0, 0)
+    try:
+        cache = build(fnr, ctx, k, l, D, pos, dirn, prec, prec)
+        sig, uvw, beta = read_cache(fnr, cache, k, D, l, prec, prec)
+        xyz = oracle.cell_centres(k, np.arange(k ** 3))
+        ref_b = oracle.mlp_eval(as_fp64(pos), xyz, 10, True)
+        got = np.concatenate([sig[:, None], uvw], axis=1)
+        ref = np.concatenate([np.maximum(ref_b[:, :1], 0), ref_b[:, 1:]], axis=1)
+        check_channels(got, ref, 5e-3 if prec == 0 else 6e-3)
+        ref64 = oracle.mlp_eval(as_fp64(pos), xyz, 10, False)
+        rel = np.linalg.norm(uvw - ref64[:, 1:]) / np.linalg.norm(ref64[:, 1:])
+        assert rel < 5e-2, rel
+        dirs = oracle.bin_directions(l, np.arange(l * l))
+        check_channels(beta, oracle.mlp_eval(as_fp64(dirn), dirs, 4, True), 5e-3 if prec == 0 else 6e-3)
+    finally:
+        fnr.fnr_context_destroy(ctx)
+
+
+def test_cache_build_config_sampled(fnr):
+    """F_pos over 512^3 and F_dir over 512^2 (He-uniform, seed 0), checked on 32768 random grid points
+    (seed 1) and 4096 random direction bins; then a render of the built cache matches the oracle."""
+    import torch
+    k, l, D = 512, 512, 8
+    pos = scenegen.mlp_weights(0, scenegen.FPOS_DIMS_D8)
+    dirn = scenegen.mlp_weights(100, scenegen.FDIR_DIMS_D8)
+    ctx = fnr.fnr_context_create(0, 0)
+    try:
+        cache = build(fnr, ctx, k, l, D, pos, dirn)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(1)
+        cells = rng.integers(0, k ** 3, 32768)
+        lay = fnr.fnr_cache_get_layout(cache)
+        sig_all = device_bytes(lay.sigma_dev, k ** 3 * 4).view(np.float32)
+        ref = oracle.mlp_eval(as_fp64(pos), oracle.cell_centres(k, cells), 10, True)
+        rec = torch.as_tensor(type("V", (), {"__cuda_array_interface__": {
+            "shape": (k ** 3, lay.record_stride // 4), "typestr": "<f4", "data": (lay.uvw_dev, False),
+            "version": 3}})(), device="cuda")
+        uvw = rec[torch.from_numpy(cells).cuda()].cpu().numpy().astype(np.float64)[:, :3 * D]
+        got = np.concatenate([sig_all[cells].astype(np.float64)[:, None], uvw], axis=1)
+        check_channels(got, np.concatenate([np.maximum(ref[:, :1], 0), ref[:, 1:]], axis=1))
+        bins = rng.integers(0, l * l, 4096)
+        beta_all = device_bytes(lay.beta_dev, l * l * D * 4).view(np.float32).reshape(l * l, D)
+        check_channels(beta_all[bins].astype(np.float64),
+                       oracle.mlp_eval(as_fp64(dirn), oracle.bin_directions(l, bins), 4, True))
+    finally:
+        fnr.fnr_context_destroy(ctx)
+
+
+def test_render_mlp_built_cache(fnr):
+    """A cache built by the MLP kernel renders like the oracle rendering the same cache values."""
+    import torch
+    k, l, D = 32, 16, 8
+    pos = scenegen.mlp_weights(5, scenegen.FPOS_DIMS_D8, bias_scale=0.5)
+    dirn = scenegen.mlp_weights(6, scenegen.FDIR_DIMS_D8, bias_scale=0.5)
+    ctx = fnr.fnr_context_create(0, 0)
+    try:
+        cache = build(fnr, ctx, k, l, D, pos, dirn)
+        sig, uvw, beta = read_cache(fnr, cache, k, D, l)
+        oc = oracle.Cache(k, D, l, sig.astype(np.float32), uvw.astype(np.float32), beta.astype(np.float32))
+        cam = scenegen.cameras(9, 1, 48, 40)[0]
+        p = fnr.make_params(64)
+        rgba = torch.zeros(48 * 40 * 4, device="cuda")
+        st = torch.zeros(48 * 40 * 4, device="cuda", dtype=torch.int32)
+        fnr.fnr_render(ctx, cache, [cam], p, rgba, st)
+        torch.cuda.synchronize()
+        ref, rst, _ = oracle.render_image(oc, cam, oracle.params_struct(64))
+        assert np.array_equal(st.cpu().numpy().reshape(40, 48, 4), rst)
+        assert np.max(np.abs(rgba.cpu().numpy().reshape(40, 48, 4) - ref)) <= 1e-5
+    finally:
+        fnr.fnr_context_destroy(ctx)
