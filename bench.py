@@ -39,6 +39,10 @@ def parse():
     ap.add_argument("--k", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="only the plain FP32 render line")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of each served run")
+    ap.add_argument("--only-build", action="store_true",
+                    help="time only the tensor-core cache build (F_pos over k^3, F_dir over 512^2)")
     return ap.parse_args()
 
 
@@ -145,6 +149,190 @@ def cpu_baseline(w, sig, uvw, beta, cams, seconds: float, seed: int = 0):
             "seconds": dt}
 
 
+RESOLUTIONS = [(256, 256), (512, 512), (800, 800), (1280, 720), (1920, 1080)]
+
+
+def psnr(a: np.ndarray, b: np.ndarray) -> float:
+    mse = float(np.mean((a - b) ** 2))
+    return float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)
+
+
+def precision_forms(fnr, torch, ctx, w, sig, uvw, beta, cams, steps, rng_seed=7):
+    """FP16 and FP8-E4M3 position caches (FP16 direction cache) of the same scene: render throughput and
+    error against the FP64 oracle (which reads the unquantised binary32 cache) on sampled pixels."""
+    import oracle
+    oc = oracle.Cache(w.k, w.D, w.l, sig, uvw, beta)
+    op = oracle.params_struct(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg)
+    rng = np.random.default_rng(rng_seed)
+    samples = []
+    for cam in cams:
+        px = rng.integers(0, w.W, 2500).astype(np.int32)
+        py = rng.integers(0, w.H, 2500).astype(np.int32)
+        ref, _, _ = oracle.render_pixels(oc, cam, op, px, py)
+        samples.append((px, py, ref))
+    params = fnr.make_params(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg)
+    fcams = [fnr.make_camera(c) for c in cams]
+    npix = w.W * w.H
+    rgba = torch.empty((len(cams), npix * 4), device="cuda", dtype=torch.float32)
+    out = {}
+    for name, prec, dprec in (("fp32", 0, 0), ("fp16", 1, 1), ("fp8_e4m3", 2, 1)):
+        desc = fnr.make_desc(w.k, w.D, w.l, prec, dprec)
+        cache = fnr.fnr_build_cache(ctx, desc, sig.reshape(-1), uvw.reshape(-1), beta.reshape(-1))
+        stream = torch.cuda.current_stream()
+        for _ in range(3):
+            for i in range(len(cams)):
+                fnr.fnr_render(ctx, cache, [fcams[i]], params, rgba[i], None, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            for i in range(len(cams)):
+                fnr.fnr_render(ctx, cache, [fcams[i]], params, rgba[i], None, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        imgs = rgba.cpu().numpy().reshape(len(cams), w.H, w.W, 4)
+        got = np.concatenate([imgs[i][py, px, :3] for i, (px, py, _) in enumerate(samples)])
+        ref = np.concatenate([r[:, :3] for _, _, r in samples])
+        out[name] = {"mrays_per_s": steps * len(cams) * npix / (ms * 1e-3) / 1e6,
+                     "frame_ms": ms / (steps * len(cams)), "cache_bytes": fnr.fnr_cache_footprint(desc),
+                     "max_abs_vs_fp64": float(np.max(np.abs(got - ref))), "psnr_db_vs_fp64": psnr(got, ref),
+                     "pixels_checked": int(got.shape[0])}
+        fnr.fnr_cache_free(ctx, cache)
+    return out
+
+
+def cache_build(fnr, torch, ctx, k=512, l=512):
+    """F_pos (8x256 ReLU + head, L=10) over k^3 cell centres and F_dir (4x128 ReLU + head, L=4) over l^2 bins,
+    bf16 on the tensor cores with fp32 accumulation; He-uniform weights, seed 0."""
+    import scenegen
+    pos = scenegen.mlp_weights(0, scenegen.FPOS_DIMS_D8)
+    dirn = scenegen.mlp_weights(100, scenegen.FDIR_DIMS_D8)
+    dev = lambda L: [(torch.from_numpy(W.view(np.int16)).cuda(), torch.from_numpy(b).cuda()) for W, b in L]
+    pl, dl = dev(pos), dev(dirn)
+    flop_pt = lambda dims: 2 * sum(a * b for a, b in zip(dims[:-1], dims[1:]))
+    flops = flop_pt(scenegen.FPOS_DIMS_D8) * k ** 3 + flop_pt(scenegen.FDIR_DIMS_D8) * l * l
+    desc = fnr.make_desc(k, 8, l)
+    times = []
+    for _ in range(2):  # first call includes one-time set-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cache = fnr.fnr_build_cache_mlp(ctx, desc, pl, dl)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        fnr.fnr_cache_free(ctx, cache)
+    peaks, kind = measured_peaks()
+    dt = min(times)
+    return {"workload": f"F_pos over {k}^3 + F_dir over {l}^2, bf16 x bf16 -> fp32", "flops": flops,
+            "seconds": dt, "tflops": flops / dt / 1e12, "peak_tflops": float(peaks["bf16_tflops"]),
+            "frac": flops / dt / 1e12 / float(peaks["bf16_tflops"]),
+            "peak_kind": f"{kind} cuBLAS bf16 (burst)",
+            "timing": "whole fnr_build_cache call (includes the cache allocation), best of 2"}
+
+
+def served_vs_plain(fnr, torch, ctx, w, sig, uvw, beta, seconds, rate_hz=400.0, seed=11):
+    """Poisson arrivals of random-camera requests with resolutions uniform over RESOLUTIONS, N=128:
+    (a) served from an FP16 cache through fnr_submit (continuous batching), (b) the plain FP32 renderer,
+    one frame per launch, one request at a time in arrival order. Open loop at rate_hz, then closed loop
+    (all requests submitted at once) for throughput."""
+    import scenegen
+    rng = np.random.default_rng(seed)
+    params = fnr.make_params(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg)
+    c16 = fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, 1, 1), sig.reshape(-1), uvw.reshape(-1),
+                              beta.reshape(-1))
+    c32 = fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, 0, 0), sig.reshape(-1), uvw.reshape(-1),
+                              beta.reshape(-1))
+    n_req = max(8, int(rate_hz * seconds))
+    specs = []
+    for i in range(n_req):
+        W, H = RESOLUTIONS[int(rng.integers(0, len(RESOLUTIONS)))]
+        specs.append(fnr.make_camera(scenegen.cameras(10000 + i, 1, W, H, hemisphere=True)[0]))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, n_req))
+    pool = {}
+    for W, H in RESOLUTIONS:
+        pool[(W, H)] = [torch.empty(W * H * 4, device="cuda") for _ in range(48)]
+    used = {k: 0 for k in pool}
+
+    def out_for(cam):
+        key = (cam.width, cam.height)
+        t = pool[key][used[key] % len(pool[key])]
+        used[key] += 1
+        return t
+
+    fnr.fnr_serve_start(ctx, n_slots=3, max_batch_requests=64, use_graphs=1)
+    torch.cuda.synchronize()
+
+    def run_served(open_loop: bool):
+        lat, t_first, t_last = [], None, None
+        tickets = []
+        t0 = time.perf_counter()
+        for i, cam in enumerate(specs):
+            if open_loop:
+                while time.perf_counter() - t0 < arrivals[i]:
+                    pass
+            tickets.append(fnr.fnr_submit(ctx, fnr.make_request(c16, cam, params, out_for(cam))))
+        for t in tickets:
+            r = fnr.fnr_wait(ctx, t, 60000)
+            lat.append((r.t_done_ns - r.t_submit_ns) * 1e-6)
+            t_first = r.t_submit_ns if t_first is None else min(t_first, r.t_submit_ns)
+            t_last = r.t_done_ns if t_last is None else max(t_last, r.t_done_ns)
+        return np.array(lat), (t_last - t_first) * 1e-9
+
+    def run_plain(open_loop: bool):
+        lat = []
+        stream = torch.cuda.current_stream()
+        t0 = time.perf_counter()
+        for i, cam in enumerate(specs):
+            if open_loop:
+                while time.perf_counter() - t0 < arrivals[i]:
+                    pass
+            arrive = t0 + arrivals[i] if open_loop else t0
+            fnr.fnr_render(ctx, c32, [cam], params, out_for(cam), None, stream=stream)
+            stream.synchronize()
+            lat.append((time.perf_counter() - arrive) * 1e3)
+        return np.array(lat), time.perf_counter() - t0
+
+    run_served(False)  # warm-up: graphs captured, kernels loaded
+    run_plain(False)
+    res = {}
+    for mode, ol in (("open_loop", True), ("closed_loop", False)):
+        ls, ts = run_served(ol)
+        lp, tp = run_plain(ol)
+        res[mode] = {
+            "served_fp16": {"p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
+                            "frames_per_s": n_req / ts},
+            "plain_fp32_per_frame": {"p50_ms": float(np.percentile(lp, 50)), "p99_ms": float(np.percentile(lp, 99)),
+                                     "frames_per_s": n_req / tp}}
+    fnr.fnr_serve_stop(ctx)
+    fnr.fnr_cache_free(ctx, c16)
+    fnr.fnr_cache_free(ctx, c32)
+    return {"requests": n_req, "rate_hz": rate_hz, "resolutions": RESOLUTIONS, "n_samples": w.n_samples,
+            "cache": f"k={w.k} D={w.D} fp16 (served) vs fp32 (plain)", **res,
+            "latency": "submit -> completion seen by the host (served); arrival -> frame synchronised (plain)"}
+
+
+def rank_views(w, rank: int) -> list:
+    """Weak scaling: every rank renders its own views of the same scene (camera seed offset by rank)."""
+    import scenegen
+    return scenegen.cameras(w.cam_seed + 1000 * rank, w.n_cams, w.W, w.H, hemisphere=True)
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Largest value over the ranks (the job's elapsed time is the slowest rank's)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, elapsed_ms: float) -> float:
+    """Whole-job throughput in millions of units per second: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / (elapsed_ms * 1e-3) / 1e6
+
+
 def make_workload(k):
     import scenegen
     return scenegen.scale(k=k)
@@ -204,8 +392,7 @@ def run_fnr(args):
     dev = torch.device("cuda", local)
 
     w = make_workload(args.k)
-    # weak scaling: every rank renders its own 8 views of the same scene
-    cams = scenegen.cameras(w.cam_seed + 1000 * rank, w.n_cams, w.W, w.H, hemisphere=True)
+    cams = rank_views(w, rank)
     sig, uvw = scenegen.fill_position_grid(w.scene, w.k)
     beta = scenegen.direction_grid(w.scene, w.l)
 
@@ -257,12 +444,8 @@ def run_fnr(args):
         torch.distributed.barrier()
     total_ms = t_start.elapsed_time(t_end)
     frame_ms = np.array([[a.elapsed_time(b) for a, b in ev] for ev in frame_events]).reshape(-1)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    rays_total = args.steps * w.n_cams * npix * world
-    value = rays_total / (total_ms * 1e-3) / 1e6
+    total_ms = reduce_max(total_ms, world, dev)
+    value = job_rate(args.steps * w.n_cams * npix, world, total_ms)
 
     # end to end through the public API with host buffers: camera structs go host -> device with each
     # launch, every frame's RGBA comes back to pinned host memory inside the timed region
@@ -308,10 +491,15 @@ def run_fnr(args):
             "clocks": clocks.summary(),
             "gpu_launches": args.steps * w.n_cams,
         }
+    fnr.fnr_cache_free(ctx, cache)
+    if rank == 0:
+        if not args.no_extras:
+            out["precision_forms"] = precision_forms(fnr, torch, ctx, w, sig, uvw, beta, cams, max(5, args.steps // 10))
+            out["served"] = served_vs_plain(fnr, torch, ctx, w, sig, uvw, beta, args.serve_seconds)
+            out["cache_build"] = cache_build(fnr, torch, ctx)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, sig, uvw, beta, cams, args.cpu_seconds)
         print(json.dumps(out), flush=True)
-    fnr.fnr_cache_free(ctx, cache)
     fnr.fnr_context_destroy(ctx)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -319,6 +507,14 @@ def run_fnr(args):
 
 def main():
     args = parse()
+    if args.only_build:
+        import torch
+        import paper_2103_10380_gb300 as fnr
+        torch.cuda.set_device(0)
+        ctx = fnr.fnr_context_create(0, 0)
+        print(json.dumps({"cache_build": cache_build(fnr, torch, ctx, k=args.k)}), flush=True)
+        fnr.fnr_context_destroy(ctx)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

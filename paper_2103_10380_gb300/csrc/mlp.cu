@@ -3,21 +3,26 @@
 // Section 3.2 Eqs. 3-4 and Section 4: F_pos and F_dir are ReLU MLPs on
 // positionally encoded inputs).
 //
-// One CTA per SM walks tiles of 128 grid points. Per tile:
-//   1. every thread encodes one point (gamma(x) = sin / cos(2^j pi x), binary32,
-//      rounded to bf16) into shared memory, in the UMMA K-major no-swizzle
-//      layout (8 x 8 core matrices, 16 bytes per core-matrix row);
-//   2. per layer: the layer's bf16 weights -- pre-arranged once in the same
-//      core-matrix layout -- arrive in shared memory by bulk async copy
-//      (cp.async.bulk, completion on an mbarrier); one elected thread issues
-//      K/16 tcgen05.mma (M=128, N=layer width, bf16 x bf16 -> fp32) into a
-//      tensor-memory accumulator and commits them to an mbarrier; four warps
-//      read the accumulator back (tcgen05.ld, one 32-lane quarter each), add
-//      the bias, apply ReLU, round to bf16 and write the next layer's input;
-//   3. the last layer's outputs go straight to the cache: sigma = ReLU(out_0),
-//      (u, v, w) = out_1..3D for F_pos; beta = out_0..D-1 for F_dir.
-// Every mbarrier wait is bounded; a wait that runs out sets the error word and
-// the CTA stops issuing work, frees its tensor memory and returns.
+// One CTA per SM walks tiles of 128 grid points with three warp roles:
+//   producer (warp 0): streams every layer's bf16 weights, pre-arranged in
+//     32-wide K chunks of the UMMA K-major no-swizzle layout, through a 4-slot
+//     shared-memory ring by bulk async copy (cp.async.bulk, completion on the
+//     slot's "full" mbarrier), running ahead across layers and tiles;
+//   two tiles are in flight: each has its own A tile and its own tensor-memory
+//     accumulator, so one tile's epilogue runs while the other's MMAs do;
+//   MMA issuer (warp 1, one lane): waits for the layer input and each chunk,
+//     issues tcgen05.mma (M=128, N=layer width, bf16 x bf16 -> fp32 in tensor
+//     memory), releases each slot with tcgen05.commit on its "empty" mbarrier
+//     and signals the finished accumulator with one more commit;
+//   epilogue (warps 4-19, four per 32-lane quarter of tensor memory): encode
+//     the tile's points (gamma(x) = sin / cos(2^j pi x), rounded to bf16) into
+//     the A tile, then per layer read the accumulator (tcgen05.ld), add the
+//     bias, apply ReLU, round to bf16 and write the next layer's A tile -- or,
+//     after the head, write sigma = ReLU(out_0), (u, v, w) = out_1..3D (F_pos)
+//     or beta = out_0..D-1 (F_dir) straight into the cache.
+// The next layer's weights load while the epilogue runs. Every mbarrier wait
+// is bounded; a wait that runs out sets the error word and a CTA-wide abort
+// flag, every role leaves its loop, and the tensor memory is freed.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -35,22 +40,31 @@ namespace {
 constexpr int kTileM = 128;
 constexpr int kMaxK = 256;
 constexpr int kMaxN = 256;
-constexpr int kThreads = 128;
+constexpr int kChunkK = 32;                          // K columns per weight chunk
+constexpr int kSlots = 4;                            // ring slots
+constexpr int kSlotBytes = kMaxN * kChunkK * 2;      // 16 KB
+constexpr int kPair = 2;                             // tiles in flight per CTA
+constexpr int kProducerWarp = 0, kMmaWarp = 1, kFirstEpiWarp = 4, kEpiWarps = 16;
+constexpr int kThreads = (kFirstEpiWarp + kEpiWarps) * 32;
 constexpr int kMaxLayers = 16;
-constexpr uint32_t kTmemCols = 256;
-constexpr size_t kSmemA = size_t(kTileM) * kMaxK * 2;   // 64 KB activations
-constexpr size_t kSmemB = size_t(kMaxN) * kMaxK * 2;    // 128 KB one layer of weights
-constexpr size_t kSmemBytes = kSmemA + kSmemB + 64;
-constexpr long long kWaitLimit = 1LL << 22;             // try_wait polls before giving up
+constexpr int kMaxBias = kMaxLayers * kMaxN;
+constexpr uint32_t kTmemCols = 256 * kPair;                                // one accumulator per tile
+constexpr size_t kSmemA = size_t(kPair) * kTileM * kMaxK * 2;               // 2 x 64 KB activations
+constexpr size_t kSmemRing = size_t(kSlots) * kSlotBytes;                   // 64 KB weights
+constexpr size_t kSmemBias = size_t(kMaxBias) * 4;                          // 16 KB biases
+constexpr size_t kSmemBytes = kSmemA + kSmemRing + kSmemBias + 256;
+constexpr long long kWaitLimit = 1LL << 22;                                 // try_wait polls before giving up
 
 struct MlpLayerDev {
-    const __nv_bfloat16 *w;  // core-matrix layout, Np x Kp
-    const float *b;          // Np (zero padded)
+    const __nv_bfloat16 *w;  // chunk-major: chunk c = [Np][kc] in core-matrix layout, chunks of Np*kChunkK elements
     int K, N;                // padded to multiples of 16
+    int bias_off;            // offset of this layer's Np biases in the bias table
 };
 
 struct MlpArgs {
     MlpLayerDev L[kMaxLayers];
+    const float *bias;       // all layers' padded biases
+    int n_bias;
     int n_layers;
     int mode;        // 0: F_pos over the k^3 cell centres, 1: F_dir over the l x l bin centres
     int pe_freqs;
@@ -88,13 +102,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: false (and the error word set) when the limit runs out.
-// Only thread 0 waits; the CTA learns the outcome through a barrier.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
-    for (long long it = 0; it < kWaitLimit; ++it)
+// Bounded wait: false when the limit runs out (the error word and the
+// CTA's abort flag are then set) or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag) {
+    for (long long it = 0; it < kWaitLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 1023) == 1023 && *abort_flag) return false;
+    }
     atomicExch(err, 1);
+    *abort_flag = 1;
     return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
@@ -156,6 +177,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 columns of this warp's TMEM lane quarter, without waiting (see tmem_wait).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // Byte offset of element (row, k) in a K-major core-matrix tile with Kp columns.
 __device__ __forceinline__ uint32_t cm_offset(int row, int k, int Kp) {
     return uint32_t((row >> 3) * (Kp >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
@@ -166,8 +198,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return uint32_t(__bfloat16_as_ushort(x)) | (uint32_t(__bfloat16_as_ushort(y)) << 16);
 }
 
-// Positional encoding of this thread's point into row `row` of the A tile.
-__device__ __forceinline__ void encode_point(const MlpArgs &A, long long p, int row, char *sa) {
+// Positional encoding of point p into row `row` of the A tile: the 8-column
+// groups g0, g0 + gstep, ... (the four epilogue warps of a row share them).
+__device__ __forceinline__ void encode_point(const MlpArgs &A, long long p, int row, char *sa, int g0, int gstep) {
     const int K0 = A.L[0].K;
     float x[3] = {0.0f, 0.0f, 0.0f};
     const bool valid = p < A.n_points;
@@ -181,15 +214,15 @@ __device__ __forceinline__ void encode_point(const MlpArgs &A, long long p, int 
         } else {
             const int it = int(p / A.l), ip = int(p % A.l);
             float st, ct, sp, cp;
-            sincospif((float(it) + 0.5f) / float(A.l), &st, &ct);          // theta / pi
-            sincospif(2.0f * (float(ip) + 0.5f) / float(A.l), &sp, &cp);   // phi / pi
+            sincospif((float(it) + 0.5f) / float(A.l), &st, &ct);         // theta / pi
+            sincospif(2.0f * (float(ip) + 0.5f) / float(A.l), &sp, &cp);  // phi / pi
             x[0] = st * cp;
             x[1] = st * sp;
             x[2] = ct;
         }
     }
     const int Lf = A.pe_freqs;
-    for (int g = 0; g < K0; g += 8) {  // 8 encoded values per 16-byte store
+    for (int g = g0 * 8; g < K0; g += gstep * 8) {  // 8 encoded values per 16-byte store
         float v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -211,22 +244,40 @@ __device__ __forceinline__ void encode_point(const MlpArgs &A, long long p, int 
     }
 }
 
+__device__ __forceinline__ int n_chunks(int K) { return (K + kChunkK - 1) / kChunkK; }
+__device__ __forceinline__ int chunk_width(int K, int c) { return min(kChunkK, K - c * kChunkK); }
+
 __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant__ MlpArgs A) {
     extern __shared__ __align__(1024) char smem[];
-    char *sa = smem;
-    char *sb = smem + kSmemA;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kSmemA + kSmemB);  // [0] weights, [1] mma
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
-    __shared__ int abort_flag;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t bar_w = smem_u32(&bars[0]), bar_m = smem_u32(&bars[1]);
+    char *sa = smem;  // A tile of slot t at sa + t * kTileM * kMaxK * 2
+    char *ring = smem + kSmemA;
+    float *sbias = reinterpret_cast<float *>(smem + kSmemA + kSmemRing);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kSmemA + kSmemRing + kSmemBias);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kSlots + 2 * kPair);
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // bars: [0, kSlots) full, [kSlots, 2 kSlots) empty, then acc_full[kPair], then a_ready[kPair]
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_bar = [&](int s) { return bar0 + 8u * uint32_t(s); };
+    auto empty_bar = [&](int s) { return bar0 + 8u * uint32_t(kSlots + s); };
+    auto acc_full = [&](int t) { return bar0 + 8u * uint32_t(2 * kSlots + t); };
+    auto a_ready = [&](int t) { return bar0 + 8u * uint32_t(2 * kSlots + kPair + t); };
+    constexpr uint32_t kATileBytes = uint32_t(kTileM) * kMaxK * 2;
 
+    for (int i = tid; i < A.n_bias; i += kThreads) sbias[i] = A.bias[i];
     if (tid == 0) {
-        mbar_init(bar_w, 1);
-        mbar_init(bar_m, 1);
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int t = 0; t < kPair; ++t) {
+            mbar_init(acc_full(t), 1);
+            mbar_init(a_ready(t), kEpiWarps);
+        }
+        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols)
                      : "memory");
@@ -236,117 +287,190 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    uint32_t ph_w = 0, ph_m = 0;
-
+    // Tiles go to CTAs in pairs: the CTA's pair r holds tiles (2r) * grid + bid and (2r + 1) * grid + bid;
+    // a tile past the end is carried as an empty one (no outputs).
     const long long n_tiles = (A.n_points + kTileM - 1) / kTileM;
-    bool aborted = false;  // uniform across the CTA: read only after a barrier
-    for (long long tile = blockIdx.x; tile < n_tiles && !aborted; tile += gridDim.x) {
-        const long long p = tile * kTileM + tid;
-        encode_point(A, p, tid, sa);
-        fence_proxy_async();
-        __syncthreads();
-        for (int li = 0; li < A.n_layers; ++li) {
-            const MlpLayerDev &Ly = A.L[li];
-            const int K = Ly.K, N = Ly.N;
-            const bool last = li + 1 == A.n_layers;
-            // Thread 0 stages the layer's weights, issues its MMAs and waits for
-            // them; the other threads learn the outcome at the barrier.
-            if (tid == 0) {
-                const uint32_t bytes = uint32_t(N) * uint32_t(K) * 2u;
-                mbar_expect_tx(bar_w, bytes);
-                const char *src = reinterpret_cast<const char *>(Ly.w);
-                for (uint32_t off = 0; off < bytes; off += 32768u) {
-                    const uint32_t chunk = bytes - off < 32768u ? bytes - off : 32768u;
-                    bulk_g2s(smem_u32(sb) + off, src + off, chunk, bar_w);
-                }
-                bool ok = mbar_wait(bar_w, ph_w, A.err);
-                if (ok) {
-                    tc_fence_after();
-                    const uint32_t idesc = instr_desc(kTileM, N);
-                    const uint32_t sbo = uint32_t(K >> 3) * 128u;
-                    for (int s = 0; s < K / 16; ++s) {
-                        const uint64_t ad = smem_desc(smem_u32(sa) + uint32_t(s) * 256u, 128u, sbo);
-                        const uint64_t bd = smem_desc(smem_u32(sb) + uint32_t(s) * 256u, 128u, sbo);
-                        umma_bf16(tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
-                    }
-                    umma_commit(bar_m);
-                    ok = mbar_wait(bar_m, ph_m, A.err);
-                }
-                abort_flag = ok ? 0 : 1;
-                tc_fence_before();
-            }
-            ph_w ^= 1u;
-            ph_m ^= 1u;
-            __syncthreads();
-            tc_fence_after();
-            if (abort_flag) {
-                aborted = true;
-                break;
-            }
-            // epilogue: this warp's 32 rows of the accumulator (warp-collective
-            // loads; stores predicated per row)
-            const uint32_t trow = tmem + (uint32_t(warp * 32) << 16);
-            const int row = tid;
-            const bool valid = p < A.n_points;
-            for (int c0 = 0; c0 < N; c0 += 16) {
-                float v[16];
-                tmem_ld16(trow + uint32_t(c0), v);
-                if (!last) {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + __ldg(Ly.b + c0 + q), 0.0f);
-#pragma unroll
-                    for (int g = 0; g < 16; g += 8) {
-                        uint4 pk;
-                        pk.x = pack_bf16(v[g + 0], v[g + 1]);
-                        pk.y = pack_bf16(v[g + 2], v[g + 3]);
-                        pk.z = pack_bf16(v[g + 4], v[g + 5]);
-                        pk.w = pack_bf16(v[g + 6], v[g + 7]);
-                        *reinterpret_cast<uint4 *>(sa + cm_offset(row, c0 + g, N)) = pk;
-                    }
-                } else if (valid) {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int c = c0 + q;
-                        const float o = v[q] + __ldg(Ly.b + c);
-                        if (A.mode == 0) {
-                            if (c == 0) {
-                                const float sg = fmaxf(o, 0.0f);
-                                if (A.prec == FNR_PREC_FP16) static_cast<__half *>(A.sigma_out)[p] = __float2half_rn(sg);
-                                else static_cast<float *>(A.sigma_out)[p] = sg;
-                            } else if (c <= 3 * A.D) {
-                                char *rec = A.uvw_out + p * A.rec_stride;
-                                if (A.prec == FNR_PREC_FP16)
-                                    reinterpret_cast<__half *>(rec)[c - 1] = __float2half_rn(o);
-                                else reinterpret_cast<float *>(rec)[c - 1] = o;
-                            }
-                        } else if (c < A.D) {
-                            if (A.dprec == FNR_PREC_FP16)
-                                static_cast<__half *>(A.beta_out)[p * A.D + c] = __float2half_rn(o);
-                            else static_cast<float *>(A.beta_out)[p * A.D + c] = o;
+    const long long G = gridDim.x;
+    auto pair_tile = [&](long long r, int t) { return (2 * r + t) * G + blockIdx.x; };
+    const long long n_pairs = (n_tiles - blockIdx.x + 2 * G - 1) / (2 * G);
+
+    if (warp == kProducerWarp) {
+        if (lane == 0) {
+            long long it = 0;
+            for (long long r = 0; r < n_pairs && !abort_flag; ++r)
+                for (int li = 0; li < A.n_layers && !abort_flag; ++li)
+                    for (int t = 0; t < kPair && !abort_flag; ++t) {
+                        const MlpLayerDev &Ly = A.L[li];
+                        const int nc = n_chunks(Ly.K);
+                        for (int c = 0; c < nc; ++c, ++it) {
+                            const int slot = int(it % kSlots);
+                            const long long round = it / kSlots;
+                            if (round > 0 &&
+                                !mbar_wait(empty_bar(slot), uint32_t((round - 1) & 1), A.err, &abort_flag))
+                                break;
+                            const uint32_t bytes = uint32_t(Ly.N) * uint32_t(chunk_width(Ly.K, c)) * 2u;
+                            mbar_expect_tx(full_bar(slot), bytes);
+                            bulk_g2s(smem_u32(ring) + uint32_t(slot) * kSlotBytes,
+                                     reinterpret_cast<const char *>(Ly.w) + size_t(c) * Ly.N * kChunkK * 2, bytes,
+                                     full_bar(slot));
                         }
                     }
+        }
+    } else if (warp == kMmaWarp) {
+        if (lane == 0) {
+            long long it = 0, uses = 0;  // uses: (layer, tile) steps per slot t, same count for both
+            for (long long r = 0; r < n_pairs && !abort_flag; ++r)
+                for (int li = 0; li < A.n_layers && !abort_flag; ++li, ++uses)
+                    for (int t = 0; t < kPair && !abort_flag; ++t) {
+                        const MlpLayerDev &Ly = A.L[li];
+                        if (!mbar_wait(a_ready(t), uint32_t(uses & 1), A.err, &abort_flag)) break;
+                        tc_fence_after();
+                        const uint32_t idesc = instr_desc(kTileM, Ly.N);
+                        const uint32_t sbo_a = uint32_t(Ly.K >> 3) * 128u;
+                        const uint32_t a_base = smem_u32(sa) + uint32_t(t) * kATileBytes;
+                        const uint32_t d_tmem = tmem + uint32_t(t * 256);
+                        const int nc = n_chunks(Ly.K);
+                        for (int c = 0; c < nc; ++c, ++it) {
+                            const int slot = int(it % kSlots);
+                            if (!mbar_wait(full_bar(slot), uint32_t((it / kSlots) & 1), A.err, &abort_flag)) break;
+                            tc_fence_after();
+                            const int kc = chunk_width(Ly.K, c);
+                            const uint32_t sbo_b = uint32_t(kc >> 3) * 128u;
+                            for (int s = 0; s < kc / 16; ++s) {
+                                const uint64_t ad = smem_desc(
+                                    a_base + uint32_t(c) * uint32_t(kChunkK / 8) * 128u + uint32_t(s) * 256u, 128u,
+                                    sbo_a);
+                                const uint64_t bd = smem_desc(
+                                    smem_u32(ring) + uint32_t(slot) * kSlotBytes + uint32_t(s) * 256u, 128u, sbo_b);
+                                umma_bf16(d_tmem, ad, bd, idesc, (c > 0 || s > 0) ? 1u : 0u);
+                            }
+                            umma_commit(empty_bar(slot));
+                        }
+                        if (abort_flag) break;
+                        umma_commit(acc_full(t));
+                    }
+        }
+    } else if (warp >= kFirstEpiWarp) {
+        const int q = warp & 3, g = (warp - kFirstEpiWarp) >> 2;  // lane quarter, column group
+        const int row = q * 32 + lane;
+        long long uses = 0;
+        bool stop = false;
+        for (long long r = 0; r < n_pairs && !stop; ++r) {
+            long long pt[kPair];
+#pragma unroll
+            for (int t = 0; t < kPair; ++t) {
+                const long long tile = pair_tile(r, t);
+                pt[t] = tile < n_tiles ? tile * kTileM + row : A.n_points;  // past the end: invalid row
+                encode_point(A, pt[t], row, sa + size_t(t) * kATileBytes, g, 4);
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(a_ready(t));
+            }
+            for (int li = 0; li < A.n_layers && !stop; ++li, ++uses) {
+                const MlpLayerDev &Ly = A.L[li];
+                const int N = Ly.N;
+                const bool last = li + 1 == A.n_layers;
+                const float *bias = sbias + Ly.bias_off;
+                for (int t = 0; t < kPair; ++t) {
+                    int ok = 1;
+                    if (lane == 0) ok = mbar_wait(acc_full(t), uint32_t(uses & 1), A.err, &abort_flag) ? 1 : 0;
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok) {
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const long long p = pt[t];
+                    const bool valid = p < A.n_points;
+                    char *sa_t = sa + size_t(t) * kATileBytes;
+                    const uint32_t trow = tmem + uint32_t(t * 256) + (uint32_t(q * 32) << 16);
+                    // this warp's 16-column chunks j = g, g+4, g+8, g+12, two loads in flight per wait
+                    const int nj = N / 16;
+                    auto process = [&](const uint32_t (&rr)[16], int j) {
+                        const int c0 = j * 16;
+                        float v[16];
+#pragma unroll
+                        for (int u = 0; u < 16; u += 4) {
+                            const float4 b4 = *reinterpret_cast<const float4 *>(bias + c0 + u);
+                            v[u + 0] = __uint_as_float(rr[u + 0]) + b4.x;
+                            v[u + 1] = __uint_as_float(rr[u + 1]) + b4.y;
+                            v[u + 2] = __uint_as_float(rr[u + 2]) + b4.z;
+                            v[u + 3] = __uint_as_float(rr[u + 3]) + b4.w;
+                        }
+                        if (!last) {
+#pragma unroll
+                            for (int u = 0; u < 16; u += 8) {
+                                uint4 pk;
+                                pk.x = pack_bf16(fmaxf(v[u + 0], 0.0f), fmaxf(v[u + 1], 0.0f));
+                                pk.y = pack_bf16(fmaxf(v[u + 2], 0.0f), fmaxf(v[u + 3], 0.0f));
+                                pk.z = pack_bf16(fmaxf(v[u + 4], 0.0f), fmaxf(v[u + 5], 0.0f));
+                                pk.w = pack_bf16(fmaxf(v[u + 6], 0.0f), fmaxf(v[u + 7], 0.0f));
+                                *reinterpret_cast<uint4 *>(sa_t + cm_offset(row, c0 + u, N)) = pk;
+                            }
+                        } else if (valid) {
+#pragma unroll
+                            for (int u = 0; u < 16; ++u) {
+                                const int c = c0 + u;
+                                const float o = v[u];
+                                if (A.mode == 0) {
+                                    if (c == 0) {
+                                        const float sg = fmaxf(o, 0.0f);
+                                        if (A.prec == FNR_PREC_FP16)
+                                            static_cast<__half *>(A.sigma_out)[p] = __float2half_rn(sg);
+                                        else static_cast<float *>(A.sigma_out)[p] = sg;
+                                    } else if (c <= 3 * A.D) {
+                                        char *rec = A.uvw_out + p * A.rec_stride;
+                                        if (A.prec == FNR_PREC_FP16)
+                                            reinterpret_cast<__half *>(rec)[c - 1] = __float2half_rn(o);
+                                        else reinterpret_cast<float *>(rec)[c - 1] = o;
+                                    }
+                                } else if (c < A.D) {
+                                    if (A.dprec == FNR_PREC_FP16)
+                                        static_cast<__half *>(A.beta_out)[p * A.D + c] = __float2half_rn(o);
+                                    else static_cast<float *>(A.beta_out)[p * A.D + c] = o;
+                                }
+                            }
+                        }
+                    };
+                    for (int j0 = g; j0 < nj; j0 += 8) {  // warp-uniform
+                        uint32_t r0[16], r1[16];
+                        const bool two = j0 + 4 < nj;
+                        tmem_ld16_nowait(trow + uint32_t(j0 * 16), r0);
+                        if (two) tmem_ld16_nowait(trow + uint32_t((j0 + 4) * 16), r1);
+                        tmem_wait();
+                        process(r0, j0);
+                        if (two) process(r1, j0 + 4);
+                    }
+                    tc_fence_before();
+                    if (!last) {
+                        fence_proxy_async();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(a_ready(t));
+                    } else {
+                        __syncwarp();
+                    }
                 }
             }
-            tc_fence_before();
-            fence_proxy_async();
-            __syncthreads();
         }
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
 }
 
-// W [N][K] row-major bf16 bits -> padded core-matrix layout [Np][Kp].
+// W [N][K] row-major bf16 bits -> padded, chunk-major core-matrix layout:
+// chunk c holds columns [kChunkK c, kChunkK c + kc) as [Np][kc] K-major core matrices.
 __global__ void relayout_kernel(const uint16_t *__restrict__ w, int N, int K, uint16_t *__restrict__ out, int Np,
                                 int Kp) {
     const int total = Np * Kp;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const int n = e / Kp, k = e - n * Kp;
         const uint16_t v = (n < N && k < K) ? w[size_t(n) * K + k] : uint16_t(0);
-        const size_t off = size_t(n >> 3) * (Kp >> 3) * 64 + size_t(k >> 3) * 64 + size_t(n & 7) * 8 + (k & 7);
+        const int c = k / kChunkK, kk = k - c * kChunkK, kc = min(kChunkK, Kp - c * kChunkK);
+        const size_t off = size_t(c) * Np * kChunkK + size_t(n >> 3) * (kc >> 3) * 64 + size_t(kk >> 3) * 64 +
+                           size_t(n & 7) * 8 + (kk & 7);
         out[off] = v;
     }
 }
@@ -409,12 +533,14 @@ fnr_status run_mlp(const fnr_mlp *m, int mode, const fnr_cache_desc &d, const Ca
         pad_bias_kernel<<<(Np + 255) / 256, 256, 0, s>>>(m->biases[i], N, bd, Np);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "MLP weight layout");
         A.L[i].w = reinterpret_cast<const __nv_bfloat16 *>(wd);
-        A.L[i].b = bd;
+        A.L[i].bias_off = int(bo);
         A.L[i].K = Kp;
         A.L[i].N = Np;
         wo += size_t(Np) * Kp;
         bo += size_t(Np);
     }
+    A.bias = static_cast<const float *>(bbuf.p);
+    A.n_bias = int(bo);
     A.n_layers = m->n_layers;
     A.mode = mode;
     A.pe_freqs = m->pe_freqs;

@@ -37,6 +37,7 @@ void budget_uncharge(fnr_context *ctx, uint64_t bytes);
 
 constexpr int kMaxBatch = 64;
 constexpr int kMaxSlots = 8;
+constexpr uint64_t kSpinAfterActivityNs = 5000000;  // keep polling 5 ms after the last event
 
 struct ServeFrame {
     CacheView c;
@@ -178,6 +179,19 @@ struct Server {
     int64_t next_batch = 0;
     std::map<int, int> grid_blocks;  // key -> persistent grid size
     fnr_status fatal = FNR_OK;
+    std::vector<cudaEvent_t> free_events;  // recycled request-ordering events
+    uint64_t last_activity_ns = 0;
+
+    cudaEvent_t take_event() {
+        if (!free_events.empty()) {
+            cudaEvent_t e = free_events.back();
+            free_events.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        return e;
+    }
 
     int grid_for(int key, ServeFn fn) {
         auto it = grid_blocks.find(key);
@@ -321,7 +335,7 @@ struct Server {
                 Request &r = reqs[s.tickets[f]];
                 if (r.ready) {
                     cudaStreamWaitEvent(s.stream, r.ready, 0);
-                    cudaEventDestroy(r.ready);
+                    free_events.push_back(r.ready);  // reusable once the wait is enqueued
                     r.ready = nullptr;
                 }
             }
@@ -356,10 +370,17 @@ struct Server {
             const bool p2 = admit_locked();
             busy = false;
             for (Slot &s : slots) busy |= s.busy;
-            if (p1 || p2) continue;
-            if (busy) {
+            const uint64_t now = now_ns();
+            if (p1 || p2) {
+                last_activity_ns = now;
+                continue;
+            }
+            // Completion words are polled, not waited on. While work is in flight,
+            // and for a short while after the last activity (requests tend to come
+            // in bursts), the thread spins; otherwise it sleeps until a submit.
+            if (busy || !pending.empty() || now - last_activity_ns < kSpinAfterActivityNs) {
                 lk.unlock();
-                std::this_thread::yield();  // completion words are polled, not waited on
+                std::this_thread::yield();
                 lk.lock();
             } else {
                 cv_sched.wait_for(lk, std::chrono::milliseconds(5));
@@ -443,6 +464,7 @@ void server_stop(fnr_context *ctx) {
         if (kv.second.status == FNR_ERR_NOT_READY) const_cast<fnr_cache *>(kv.second.req.cache)->inflight.fetch_sub(1);
         if (kv.second.ready) cudaEventDestroy(kv.second.ready);
     }
+    for (cudaEvent_t e : sv->free_events) cudaEventDestroy(e);
     delete sv;
     ctx->server = nullptr;
 }
@@ -514,10 +536,9 @@ fnr_status fnr_submit(fnr_context *ctx, const fnr_request *req, uint64_t *ticket
             return fail(FNR_ERR_QUEUE_FULL, "request queue is full (%d)", sv->cfg.queue_capacity);
         cudaError_t e = cudaSetDevice(ctx->device);
         if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
-        if ((e = cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming)) != cudaSuccess)
-            return cuda_fail(e, "request event");
+        if (!(r.ready = sv->take_event())) return fail(FNR_ERR_CUDA, "request event");
         if ((e = cudaEventRecord(r.ready, reinterpret_cast<cudaStream_t>(req->stream))) != cudaSuccess) {
-            cudaEventDestroy(r.ready);
+            sv->free_events.push_back(r.ready);
             return cuda_fail(e, "request event record");
         }
         r.t_submit = now_ns();
@@ -556,6 +577,17 @@ fnr_status fnr_wait(fnr_context *ctx, uint64_t ticket, uint32_t timeout_ms, fnr_
     auto it = sv->reqs.find(ticket);
     if (it == sv->reqs.end()) return fail(FNR_ERR_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    // Poll the completion words directly for a short while (low latency), then sleep.
+    const auto spin_until = std::chrono::steady_clock::now() + std::chrono::microseconds(2000);
+    while (it->second.status == FNR_ERR_NOT_READY && std::chrono::steady_clock::now() < spin_until &&
+           std::chrono::steady_clock::now() < deadline) {
+        sv->poll_locked();
+        if (it->second.status != FNR_ERR_NOT_READY) break;
+        lk.unlock();
+        std::this_thread::yield();
+        lk.lock();
+        it = sv->reqs.find(ticket);
+    }
     while (it->second.status == FNR_ERR_NOT_READY) {
         if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
             it = sv->reqs.find(ticket);
