@@ -20,7 +20,7 @@ namespace {
 using namespace dev;
 
 template <int PREC, int D>
-__global__ void __launch_bounds__(FNR_BLOCK, FNR_MINB) march_kernel(const __grid_constant__ MarchArgs A) {
+__global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC)) march_kernel(const __grid_constant__ MarchArgs A) {
     const int tile = static_cast<int>((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (tile >= A.total_tiles) return;  // whole warp
     int f = 0;

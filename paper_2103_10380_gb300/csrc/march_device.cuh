@@ -14,6 +14,8 @@ namespace dev {
 // Tuning knobs (defaults are the measured best; see the design notes):
 //   FNR_UNROLL    density loads issued together per lane
 //   FNR_BLOCK / FNR_MINB  threads per block / minimum resident blocks per SM
+//   FNR_MINB_FP16 / FNR_MINB_FP8  the same for the quantised caches (FP8 keeps
+//                 the per-channel scales folded into beta and needs more registers)
 //   FNR_FAST_EXP  1: exponentials of the occupied-sample path via ex2.approx
 //   FNR_QUEUE     1: lanes march density only and queue occupied samples; the
 //                 warp shades 32 queued samples at a time (march_tile_queued)
@@ -24,7 +26,13 @@ namespace dev {
 #define FNR_BLOCK 128
 #endif
 #ifndef FNR_MINB
-#define FNR_MINB 8
+#define FNR_MINB 7
+#endif
+#ifndef FNR_MINB_FP16
+#define FNR_MINB_FP16 8
+#endif
+#ifndef FNR_MINB_FP8
+#define FNR_MINB_FP8 8
 #endif
 #ifndef FNR_FAST_EXP
 #define FNR_FAST_EXP 1
@@ -33,6 +41,10 @@ namespace dev {
 #define FNR_QUEUE 1
 #endif
 constexpr int kUnroll = FNR_UNROLL;
+// minimum resident blocks per SM of the march kernels for a cache precision
+__host__ __device__ constexpr int min_blocks(int prec) {
+    return prec == FNR_PREC_FP8_E4M3 ? FNR_MINB_FP8 : (prec == FNR_PREC_FP16 ? FNR_MINB_FP16 : FNR_MINB);
+}
 
 __device__ __forceinline__ float e4m3_to_float(unsigned int byte) {
     __half_raw h = __nv_cvt_fp8_to_halfraw(static_cast<__nv_fp8_storage_t>(byte), __NV_E4M3);
@@ -153,6 +165,7 @@ struct RaySetup {
     float bw[NB];  // beta (FP8: beta_i * scale of channel (ch, i))
     float e[3], f[3];
     int i_lo, i_hi;
+    int in_lo, in_hi;  // samples certainly inside the box (the exact test is then redundant)
     int dcell;
     float sigma_scale;
 
@@ -210,8 +223,10 @@ struct RaySetup {
             if (e[a] == 0.0f) {
                 if (!(f[a] >= -1.0f && f[a] <= c.kf + 1.0f)) i_hi = 0;
             } else {
-                const float ta = (-1.0f - f[a]) / e[a] - 0.5f;
-                const float tb = (c.kf + 1.0f - f[a]) / e[a] - 0.5f;
+                // approximate reciprocal: these bounds carry two samples of margin
+                const float re = __frcp_rn(e[a]);
+                const float ta = (-1.0f - f[a]) * re - 0.5f;
+                const float tb = (c.kf + 1.0f - f[a]) * re - 0.5f;
                 const float lo = fmaxf(fminf(ta, tb) - 2.0f, -1.0f);
                 const float hi = fminf(fmaxf(ta, tb) + 2.0f, static_cast<float>(r.N) + 1.0f);
                 i_lo = max(i_lo, __float2int_rd(lo));
@@ -219,6 +234,28 @@ struct RaySetup {
             }
         }
         i_lo = min(i_lo, r.N);
+        // The same bound narrowed by one cell on every face and two samples at
+        // each end: samples in [in_lo, in_hi) have 1 <= g_a <= k - 1 on every axis
+        // with room to spare for the rounding of g and of these bounds, so the
+        // exact per-sample test would pass there.
+        in_lo = 0;
+        in_hi = finite_dir ? r.N : 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (e[a] == 0.0f) {
+                if (!(f[a] >= 1.0f && f[a] <= c.kf - 1.0f)) in_hi = 0;
+            } else {
+                const float re = __frcp_rn(e[a]);
+                const float ta = (1.0f - f[a]) * re - 0.5f;
+                const float tb = (c.kf - 1.0f - f[a]) * re - 0.5f;
+                const float lo = fminf(fmaxf(fminf(ta, tb) + 2.0f, -1.0f), static_cast<float>(r.N) + 1.0f);
+                const float hi = fmaxf(fminf(fmaxf(ta, tb) - 2.0f, static_cast<float>(r.N) + 1.0f), -1.0f);
+                in_lo = max(in_lo, __float2int_ru(lo));
+                in_hi = min(in_hi, __float2int_rd(hi));
+            }
+        }
+        in_lo = max(in_lo, i_lo);
+        in_hi = min(in_hi, i_hi);
     }
 
     // Cell of sample i (fi = i + 0.5) or -1 outside the box. For finite g,
@@ -234,13 +271,27 @@ struct RaySetup {
         return in ? (iz * c.k + iy) * c.k + ix : -1;  // k^3 < 2^31
     }
 
+    // Cell of a sample known to be inside the box.
+    __device__ __forceinline__ int cell_inside(const CacheView &c, float fi) const {
+        const int ix = __float2int_rd(__fmaf_rn(fi, e[0], f[0]));
+        const int iy = __float2int_rd(__fmaf_rn(fi, e[1], f[1]));
+        const int iz = __float2int_rd(__fmaf_rn(fi, e[2], f[2]));
+        return (iz * c.k + iy) * c.k + ix;
+    }
+
     // a7: Eq. 5 and the activation for one record.
     __device__ __forceinline__ void shade(const Record<PREC, D> &rec, int act, const float *b, float col[3]) const {
+        shade_with(rec, act, [&](int ch, int j) { return b[(PREC == FNR_PREC_FP8_E4M3) ? ch * D + j : j]; }, col);
+    }
+    // the same with beta_j (times the FP8 scale of channel (ch, j)) supplied by beta_of(ch, j)
+    template <class BetaOf>
+    __device__ __forceinline__ static void shade_with(const Record<PREC, D> &rec, int act, BetaOf beta_of,
+                                                      float col[3]) {
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             float x = 0.0f;
 #pragma unroll
-            for (int j = 0; j < D; ++j) x = __fmaf_rn(b[(PREC == FNR_PREC_FP8_E4M3) ? ch * D + j : j], rec.get(ch * D + j), x);
+            for (int j = 0; j < D; ++j) x = __fmaf_rn(beta_of(ch, j), rec.get(ch * D + j), x);
 #if FNR_FAST_EXP
             col[ch] = act == FNR_ACT_IDENTITY ? x : __fdividef(1.0f, 1.0f + __expf(-x));
 #else
@@ -414,18 +465,17 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
             own = q.owner[e];
             Record<PREC, D> rec;
             rec.load(c.uvw + static_cast<long long>(q.cell[e]) * c.rec_stride);
-            float b[RaySetup<PREC, D>::NB];
+            if constexpr (PREC == FNR_PREC_FP8_E4M3) {
+                // scaled beta formed at its use: keeps 3D products out of registers
+                RaySetup<PREC, D>::shade_with(
+                    rec, r.act, [&](int ch, int j) { return q.beta[j][own] * __ldg(c.scales + 1 + ch * D + j); },
+                    col);
+            } else {
+                float b[D];
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                const float bi = q.beta[i][own];
-                if constexpr (PREC == FNR_PREC_FP8_E4M3) {
-#pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) b[ch * D + i] = bi * __ldg(c.scales + 1 + ch * D + i);
-                } else {
-                    b[i] = bi;
-                }
+                for (int i = 0; i < D; ++i) b[i] = q.beta[i][own];
+                R.shade(rec, r.act, b, col);
             }
-            R.shade(rec, r.act, b, col);
         }
         q.col[0][lane] = col[0];
         q.col[1][lane] = col[1];
@@ -456,18 +506,35 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
         int cell[kUnroll];
         float sg[kUnroll];
         float fi = __fadd_rn(static_cast<float>(i0), 0.5f);
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            cell[u] = ((vis >> u) & 1u) ? R.cell_of(c, fi) : -1;
-            fi = __fadd_rn(fi, 1.0f);
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) sg[u] = cell[u] >= 0 ? load_sigma<PREC>(c, cell[u], R.sigma_scale) : 0.0f;
         unsigned in_m = 0u, occ_m = 0u;
+        // Groups certainly inside the box for every lane still marching take the
+        // path without per-sample range tests (warp-uniform choice).
+        const bool inside = done || (i0 >= R.in_lo && i0 + kUnroll <= R.in_hi);
+        if (__all_sync(FULL, inside)) {
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            in_m |= (cell[u] >= 0 ? 1u : 0u) << u;
-            occ_m |= (sg[u] > 0.0f ? 1u : 0u) << u;
+            for (int u = 0; u < kUnroll; ++u) {
+                cell[u] = R.cell_inside(c, fi);
+                fi = __fadd_rn(fi, 1.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) sg[u] = !done ? load_sigma<PREC>(c, cell[u], R.sigma_scale) : 0.0f;
+            in_m = vis;  // every visited sample of the group is in the box
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) occ_m |= (sg[u] > 0.0f ? 1u : 0u) << u;
+        } else {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                cell[u] = ((vis >> u) & 1u) ? R.cell_of(c, fi) : -1;
+                fi = __fadd_rn(fi, 1.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                sg[u] = cell[u] >= 0 ? load_sigma<PREC>(c, cell[u], R.sigma_scale) : 0.0f;
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                in_m |= (cell[u] >= 0 ? 1u : 0u) << u;
+                occ_m |= (sg[u] > 0.0f ? 1u : 0u) << u;
+            }
         }
         if (cells_out) {
 #pragma unroll

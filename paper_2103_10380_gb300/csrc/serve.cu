@@ -79,7 +79,7 @@ __device__ __forceinline__ int serve_frame_of(const ServeTable *tab, int nf, int
 }
 
 template <int PREC, int D>
-__global__ void __launch_bounds__(FNR_BLOCK, FNR_MINB)
+__global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
     serve_kernel(const ServeTable *__restrict__ tab, ServeScratch *scr, volatile uint32_t *done_flags) {
     constexpr int kWarps = FNR_BLOCK / 32;
     __shared__ dev::WarpQueue<D> queues[kWarps];
