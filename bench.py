@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="only the plain FP32 render line")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of each served run")
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="arrival window per request rate in the serving workload (its full length is 30)")
     ap.add_argument("--only-build", action="store_true",
                     help="time only the tensor-core cache build (F_pos over k^3, F_dir over 512^2)")
     return ap.parse_args()
@@ -202,6 +203,93 @@ def precision_forms(fnr, torch, ctx, w, sig, uvw, beta, cams, steps, rng_seed=7)
     return out
 
 
+def precision_config(fnr, torch, dev, repeats=5, pix_per_view=20000, rng_seed=7):
+    """The precision workload: the scene family at k=1024^3, D=8, position cache in FP16 (53.7 GB) and in
+    E4M3 with 25 per-channel scales (26.8 GB), 768x768 FP16 direction cache, 16 views of 800x800, N=192.
+    Per view: max abs error and PSNR of sampled pixels against the FP64 oracle reading the unquantised
+    binary32 field (the oracle's tabled render: dense sigma plane, uvw evaluated for the cells rays shade),
+    plus render throughput (one view per launch). The binary32 source arrays (107 GB) live on the device
+    only while the two caches are built."""
+    import oracle
+    import scenegen
+    w = scenegen.precision()
+    k, D, l = w.k, w.D, w.l
+    t0 = time.perf_counter()
+    dsig = torch.empty(k ** 3, device=dev, dtype=torch.float32)
+    duvw = torch.empty(k ** 3 * 3 * D, device=dev, dtype=torch.float32)
+    sig_host = np.empty(k ** 3, dtype=np.float32)
+    scenegen.fill_position_grid_device(w.scene, k, dsig, duvw, sig_host)
+    beta = scenegen.direction_grid(w.scene, l)
+    dbeta = torch.from_numpy(beta.reshape(-1)).to(dev)
+    t_gen = time.perf_counter() - t0
+    cams = w.cameras()
+    fcams = [fnr.make_camera(c) for c in cams]
+    params = fnr.make_params(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg)
+    npix = w.W * w.H
+    rgba = torch.empty((len(cams), npix * 4), device=dev, dtype=torch.float32)
+    stats = torch.empty((len(cams), npix * 4), device=dev, dtype=torch.int32)
+    ctx = fnr.fnr_context_create(dev.index or 0, 0)
+    stream = torch.cuda.current_stream(dev)
+    images = {}
+    out = {"workload": w.name, "k": k, "D": D, "l": l, "n_samples": w.n_samples, "views": len(cams),
+           "source_generation_s": t_gen}
+    for name, prec in (("fp16", fnr.FNR_PREC_FP16), ("fp8_e4m3", fnr.FNR_PREC_FP8_E4M3)):
+        desc = fnr.make_desc(k, D, l, prec, fnr.FNR_PREC_FP16)
+        tb = time.perf_counter()
+        cache = fnr.fnr_build_cache(ctx, desc, dsig, duvw, dbeta, stream=stream)
+        torch.cuda.synchronize(dev)
+        t_build = time.perf_counter() - tb
+        for i in range(len(cams)):
+            fnr.fnr_render(ctx, cache, [fcams[i]], params, rgba[i], stats[i], stream=stream)
+        torch.cuda.synchronize(dev)
+        images[name] = (rgba.cpu().numpy().reshape(len(cams), w.H, w.W, 4),
+                        stats.cpu().numpy().reshape(len(cams), w.H, w.W, 4))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(repeats * len(cams))]
+        for r in range(repeats):
+            for i in range(len(cams)):
+                a, b = ev[r * len(cams) + i]
+                a.record(stream)
+                fnr.fnr_render(ctx, cache, [fcams[i]], params, rgba[i], None, stream=stream)
+                b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        out[name] = {"cache_bytes": fnr.fnr_cache_footprint(desc), "build_s": t_build,
+                     "mrays_per_s": npix / (ms.mean() * 1e-3) / 1e6, "fps": 1e3 / ms.mean(),
+                     "frame_ms_p50": float(np.percentile(ms, 50)), "frame_ms_p99": float(np.percentile(ms, 99))}
+        fnr.fnr_cache_free(ctx, cache)
+    del dsig, duvw
+    torch.cuda.empty_cache()
+    fnr.fnr_context_destroy(ctx)
+    # FP64 oracle on sampled pixels of every view
+    to = time.perf_counter()
+    rng = np.random.default_rng(rng_seed)
+    op = oracle.params_struct(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg)
+    per_view = {n: [] for n in images}
+    stats_equal_fp16 = True
+    n_cells = 0
+    for i, cam in enumerate(cams):
+        px = rng.integers(0, w.W, pix_per_view).astype(np.int32)
+        py = rng.integers(0, w.H, pix_per_view).astype(np.int32)
+        ref, ref_st, nc = oracle.render_pixels_tabled(
+            k, D, l, sig_host, beta, lambda c: scenegen.cell_records(w.scene, k, c), cam, op, px, py)
+        n_cells += nc
+        for name, (img, st) in images.items():
+            got = img[i][py, px, :3]
+            per_view[name].append((float(np.max(np.abs(got - ref[:, :3]))), psnr(got, ref[:, :3])))
+        # sigma is 0 or 50 in this scene family, both exact in FP16: the integer outputs must match
+        stats_equal_fp16 &= bool(np.array_equal(images["fp16"][1][i][py, px], ref_st))
+    for name in images:
+        errs = np.array(per_view[name])
+        out[name].update({"max_abs_vs_fp64": float(errs[:, 0].max()), "psnr_db_min": float(errs[:, 1].min()),
+                          "psnr_db_mean": float(errs[:, 1].mean()),
+                          "per_view_psnr_db": [round(float(v), 2) for v in errs[:, 1]]})
+    out["fp16"]["stats_bit_exact_vs_oracle"] = stats_equal_fp16
+    out["oracle"] = {"pixels_per_view": pix_per_view, "shaded_cells_evaluated": n_cells,
+                     "seconds": time.perf_counter() - to, "reads": "binary32 field (unquantised)"}
+    return out
+
+
 def cache_build(fnr, torch, ctx, k=512, l=512):
     """F_pos (8x256 ReLU + head, L=10) over k^3 cell centres and F_dir (4x128 ReLU + head, L=4) over l^2 bins,
     bf16 on the tensor cores with fp32 accumulation; He-uniform weights, seed 0."""
@@ -230,28 +318,39 @@ def cache_build(fnr, torch, ctx, k=512, l=512):
             "timing": "whole fnr_build_cache call (includes the cache allocation), best of 2"}
 
 
-def served_vs_plain(fnr, torch, ctx, w, sig, uvw, beta, seconds, rate_hz=400.0, seed=11):
-    """Poisson arrivals of random-camera requests with resolutions uniform over RESOLUTIONS, N=128:
-    (a) served from an FP16 cache through fnr_submit (continuous batching), (b) the plain FP32 renderer,
-    one frame per launch, one request at a time in arrival order. Open loop at rate_hz, then closed loop
-    (all requests submitted at once) for throughput."""
+RATES = (50.0, 100.0, 200.0, 400.0)
+
+
+def serving_config(fnr, torch, dev, w, sig, uvw, beta, seconds, rates=RATES, seed=11, budget=120e9):
+    """The serving workload: three resident scenes (seeds 0, 1, 2; k=512^3, D=8, 512^2 direction grid),
+    each with an FP16 and an E4M3 position cache (served; FP16 direction cache) and an FP32 one (plain),
+    all inside one context with a 120 GB HBM budget. Poisson arrivals at each rate for `seconds`; every
+    request draws a scene, an upper-hemisphere camera and a resolution from RESOLUTIONS, N=128.
+    Served: fnr_submit (continuous batching into graph launches). Plain: fnr_render, one frame per
+    launch, one request at a time in arrival order (latency counts the wait for earlier requests).
+    Then closed loop (every request of the highest rate submitted at once) for throughput."""
     import scenegen
-    rng = np.random.default_rng(seed)
+    ctx = fnr.fnr_context_create(dev.index or 0, int(budget))
     params = fnr.make_params(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg)
-    c16 = fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, 1, 1), sig.reshape(-1), uvw.reshape(-1),
-                              beta.reshape(-1))
-    c32 = fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, 0, 0), sig.reshape(-1), uvw.reshape(-1),
-                              beta.reshape(-1))
-    n_req = max(8, int(rate_hz * seconds))
-    specs = []
-    for i in range(n_req):
-        W, H = RESOLUTIONS[int(rng.integers(0, len(RESOLUTIONS)))]
-        specs.append(fnr.make_camera(scenegen.cameras(10000 + i, 1, W, H, hemisphere=True)[0]))
-    arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, n_req))
-    pool = {}
-    for W, H in RESOLUTIONS:
-        pool[(W, H)] = [torch.empty(W * H * 4, device="cuda") for _ in range(48)]
-    used = {k: 0 for k in pool}
+    caches = {"fp16": [], "fp8_e4m3": [], "fp32": []}
+    forms = (("fp16", fnr.FNR_PREC_FP16, fnr.FNR_PREC_FP16), ("fp8_e4m3", fnr.FNR_PREC_FP8_E4M3, fnr.FNR_PREC_FP16),
+             ("fp32", fnr.FNR_PREC_FP32, fnr.FNR_PREC_FP32))
+    t0 = time.perf_counter()
+    for scene_seed in (0, 1, 2):
+        if scene_seed == 0:
+            s_, u_, b_ = sig, uvw, beta
+        else:
+            ws = scenegen.scale(seed=scene_seed)
+            s_, u_ = scenegen.fill_position_grid(ws.scene, ws.k)
+            b_ = scenegen.direction_grid(ws.scene, ws.l)
+        for name, prec, dprec in forms:
+            caches[name].append(fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, prec, dprec),
+                                                    s_.reshape(-1), u_.reshape(-1), b_.reshape(-1)))
+        del s_, u_, b_
+    t_setup = time.perf_counter() - t0
+    resident = fnr.fnr_context_used_bytes(ctx)
+    pool = {(W, H): [torch.empty(W * H * 4, device=dev) for _ in range(48)] for W, H in RESOLUTIONS}
+    used = {key: 0 for key in pool}
 
     def out_for(cam):
         key = (cam.width, cam.height)
@@ -259,55 +358,80 @@ def served_vs_plain(fnr, torch, ctx, w, sig, uvw, beta, seconds, rate_hz=400.0, 
         used[key] += 1
         return t
 
-    fnr.fnr_serve_start(ctx, n_slots=3, max_batch_requests=64, use_graphs=1)
-    torch.cuda.synchronize()
+    def workload(rate, rng):
+        n = max(8, int(rate * seconds))
+        reqs = []
+        for i in range(n):
+            W, H = RESOLUTIONS[int(rng.integers(0, len(RESOLUTIONS)))]
+            cam = fnr.make_camera(scenegen.cameras(int(rng.integers(1, 2 ** 31)), 1, W, H, hemisphere=True)[0])
+            reqs.append((int(rng.integers(0, 3)), cam))
+        return reqs, np.cumsum(rng.exponential(1.0 / rate, n))
 
-    def run_served(open_loop: bool):
-        lat, t_first, t_last = [], None, None
+    def run_served(form, reqs, arrivals):
         tickets = []
         t0 = time.perf_counter()
-        for i, cam in enumerate(specs):
-            if open_loop:
+        for i, (sc, cam) in enumerate(reqs):
+            if arrivals is not None:
                 while time.perf_counter() - t0 < arrivals[i]:
                     pass
-            tickets.append(fnr.fnr_submit(ctx, fnr.make_request(c16, cam, params, out_for(cam))))
+            tickets.append(fnr.fnr_submit(ctx, fnr.make_request(caches[form][sc], cam, params, out_for(cam))))
+        lat, t_first, t_last = [], None, None
         for t in tickets:
             r = fnr.fnr_wait(ctx, t, 60000)
+            if r.status != 0:
+                raise RuntimeError(f"served request failed with status {r.status}")
             lat.append((r.t_done_ns - r.t_submit_ns) * 1e-6)
             t_first = r.t_submit_ns if t_first is None else min(t_first, r.t_submit_ns)
             t_last = r.t_done_ns if t_last is None else max(t_last, r.t_done_ns)
         return np.array(lat), (t_last - t_first) * 1e-9
 
-    def run_plain(open_loop: bool):
+    def run_plain(reqs, arrivals):
         lat = []
-        stream = torch.cuda.current_stream()
+        stream = torch.cuda.current_stream(dev)
         t0 = time.perf_counter()
-        for i, cam in enumerate(specs):
-            if open_loop:
+        for i, (sc, cam) in enumerate(reqs):
+            if arrivals is not None:
                 while time.perf_counter() - t0 < arrivals[i]:
                     pass
-            arrive = t0 + arrivals[i] if open_loop else t0
-            fnr.fnr_render(ctx, c32, [cam], params, out_for(cam), None, stream=stream)
+            arrive = t0 + (arrivals[i] if arrivals is not None else 0.0)
+            fnr.fnr_render(ctx, caches["fp32"][sc], [cam], params, out_for(cam), None, stream=stream)
             stream.synchronize()
             lat.append((time.perf_counter() - arrive) * 1e3)
         return np.array(lat), time.perf_counter() - t0
 
-    run_served(False)  # warm-up: graphs captured, kernels loaded
-    run_plain(False)
+    def summary(lat, span, n):
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "frames_per_s": n / span}
+
+    fnr.fnr_serve_start(ctx, n_slots=3, max_batch_requests=64, use_graphs=1)
+    torch.cuda.synchronize(dev)
+    rng = np.random.default_rng(seed)
+    warm, _ = workload(200.0, rng)
+    for form in ("fp16", "fp8_e4m3"):
+        run_served(form, warm, None)  # graphs captured, kernels loaded
+    run_plain(warm, None)
     res = {}
-    for mode, ol in (("open_loop", True), ("closed_loop", False)):
-        ls, ts = run_served(ol)
-        lp, tp = run_plain(ol)
-        res[mode] = {
-            "served_fp16": {"p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
-                            "frames_per_s": n_req / ts},
-            "plain_fp32_per_frame": {"p50_ms": float(np.percentile(lp, 50)), "p99_ms": float(np.percentile(lp, 99)),
-                                     "frames_per_s": n_req / tp}}
+    for rate in rates:
+        reqs, arrivals = workload(rate, rng)
+        row = {"requests": len(reqs)}
+        for form in ("fp16", "fp8_e4m3"):
+            row["served_" + form] = summary(*run_served(form, reqs, arrivals), len(reqs))
+        row["plain_fp32_per_frame"] = summary(*run_plain(reqs, arrivals), len(reqs))
+        res[f"{int(rate)}_req_per_s"] = row
+    reqs, _ = workload(max(rates), rng)
+    row = {"requests": len(reqs)}
+    for form in ("fp16", "fp8_e4m3"):
+        row["served_" + form] = summary(*run_served(form, reqs, None), len(reqs))
+    row["plain_fp32_per_frame"] = summary(*run_plain(reqs, None), len(reqs))
+    res["closed_loop"] = row
     fnr.fnr_serve_stop(ctx)
-    fnr.fnr_cache_free(ctx, c16)
-    fnr.fnr_cache_free(ctx, c32)
-    return {"requests": n_req, "rate_hz": rate_hz, "resolutions": RESOLUTIONS, "n_samples": w.n_samples,
-            "cache": f"k={w.k} D={w.D} fp16 (served) vs fp32 (plain)", **res,
+    for lst in caches.values():
+        for c in lst:
+            fnr.fnr_cache_free(ctx, c)
+    fnr.fnr_context_destroy(ctx)
+    return {"scenes": 3, "hbm_budget_bytes": int(budget), "resident_cache_bytes": int(resident),
+            "seconds_per_rate": seconds, "resolutions": RESOLUTIONS, "n_samples": w.n_samples,
+            "setup_s": t_setup, **res,
             "latency": "submit -> completion seen by the host (served); arrival -> frame synchronised (plain)"}
 
 
@@ -495,7 +619,8 @@ def run_fnr(args):
     if rank == 0:
         if not args.no_extras:
             out["precision_forms"] = precision_forms(fnr, torch, ctx, w, sig, uvw, beta, cams, max(5, args.steps // 10))
-            out["served"] = served_vs_plain(fnr, torch, ctx, w, sig, uvw, beta, args.serve_seconds)
+            out["serving"] = serving_config(fnr, torch, dev, w, sig, uvw, beta, args.serve_seconds)
+            out["precision_k1024"] = precision_config(fnr, torch, dev)
             out["cache_build"] = cache_build(fnr, torch, ctx)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, sig, uvw, beta, cams, args.cpu_seconds)

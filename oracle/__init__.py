@@ -90,6 +90,8 @@ def lib():
         L.orc_posenc.restype = None
         L.orc_mlp_forward.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_int64, P, P, ctypes.c_int]
         L.orc_mlp_forward.restype = ctypes.c_int
+        L.orc_table_field.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P]
+        L.orc_table_field.restype = None
         _lib = L
     return _lib
 
@@ -171,6 +173,39 @@ def render_pixels(cache: Cache, cam: dict, params: _Params, px, py, want_cells=F
     if rc != 0:
         raise ValueError("orc_render_pixels rejected its arguments")
     return rgba, stats, cells
+
+
+class _Table(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_void_p), ("n", ctypes.c_int64), ("cells", ctypes.c_void_p),
+                ("rec", ctypes.c_void_p), ("nch", ctypes.c_int32), ("missing", ctypes.c_int64)]
+
+
+def render_pixels_tabled(k, D, l, sigma, beta, records, cam: dict, params: _Params, px, py, nthreads=None,
+                         bmin=(-1.5, -1.5, -1.5), bmax=(1.5, 1.5, 1.5)):
+    """render_pixels for an FP32 grid whose uvw channels are too large to hold densely.
+
+    sigma: dense float32 [k^3]; beta: float32 [l, l, D]; records(cells) -> float32 [n, 3D], the uvw
+    values of the given ascending int64 cells (e.g. the scene generator evaluated at their centres).
+    First pass: the cells the rays shade (they depend on sigma alone). Second pass: the render with
+    those records. Returns (rgba [n,4] f64, stats [n,4] i32, number of distinct shaded cells).
+    """
+    sigma = np.ascontiguousarray(sigma, dtype=np.float32).reshape(-1)
+    assert sigma.size == k ** 3
+    L = lib()
+    fn = ctypes.cast(L.orc_table_field, ctypes.c_void_p).value
+    t = _Table()
+    t.sigma, t.n, t.cells, t.rec, t.nch, t.missing = sigma.ctypes.data, 0, None, None, 3 * D, 0
+    c = Cache(k, D, l, None, None, beta, bmin=bmin, bmax=bmax, field=(fn, ctypes.addressof(t)))
+    _, _, cells = render_pixels(c, cam, params, px, py, want_cells=True, nthreads=nthreads)
+    cells = cells.reshape(-1)
+    cells = cells[cells >= 0].astype(np.int64)
+    cells = np.unique(cells[sigma[cells] > 0.0])
+    rec = np.ascontiguousarray(records(cells), dtype=np.float32).reshape(cells.size, 3 * D)
+    t.n, t.cells, t.rec, t.missing = cells.size, cells.ctypes.data, rec.ctypes.data, 0
+    rgba, stats, _ = render_pixels(c, cam, params, px, py, nthreads=nthreads)
+    if t.missing != 0:
+        raise RuntimeError(f"{t.missing} shaded cells were missing from the record table")
+    return rgba, stats, int(cells.size)
 
 
 def render_image(cache: Cache, cam: dict, params: _Params, want_cells=False, nthreads=None):

@@ -289,6 +289,40 @@ static void cache_uvw(const orc_cache *c, int64_t cell, double *out) {
         out[j] = stored_scalar(c->pos_prec, c->uvw, cell * n + j, c->pos_prec == ORC_FP8 ? c->scales[1 + j] : 1.0f);
 }
 
+/* ------------------------------------------------------------ cell table
+ * A field accessor for grids too large to hold densely on the host: a dense
+ * binary32 sigma plane plus binary32 uvw records for a listed set of cells
+ * (ascending cell index). The cells a ray shades and its termination depend on
+ * sigma alone, so a first pass with an empty table lists them (its colours are
+ * discarded) and a second pass reads their records. A cell missing from the
+ * table reads as uvw = 0 and is counted. Storage only: the values returned are
+ * exactly those a dense FP32 cache would give. */
+typedef struct {
+    const float *sigma;   /* [k^3] */
+    int64_t n;            /* cells in the table */
+    const int64_t *cells; /* [n], ascending */
+    const float *rec;     /* [n][nch] */
+    int32_t nch;
+    int64_t missing;      /* uvw reads of cells not in the table */
+} orc_table;
+
+void orc_table_field(int64_t cell, int want_uvw, double *sigma, double *uvw, void *user) {
+    orc_table *t = (orc_table *)user;
+    *sigma = (double)t->sigma[cell];
+    if (!want_uvw) return;
+    int64_t lo = 0, hi = t->n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (t->cells[mid] < cell) lo = mid + 1; else hi = mid;
+    }
+    if (lo < t->n && t->cells[lo] == cell) {
+        for (int j = 0; j < t->nch; ++j) uvw[j] = (double)t->rec[lo * t->nch + j];
+    } else {
+        for (int j = 0; j < t->nch; ++j) uvw[j] = 0.0;
+        __atomic_fetch_add(&t->missing, 1, __ATOMIC_RELAXED);
+    }
+}
+
 /* ------------------------------------------------------------ one ray */
 typedef struct {
     const orc_cache *c;

@@ -334,6 +334,61 @@ def scale(seed: int = 0, k: int = 512, l: int = 512, W: int = 800, H: int = 800,
                     n_cams=n_cams, cam_seed=seed + 1, hemisphere=True)
 
 
+def precision(seed: int = 0) -> Workload:
+    """The same scene family at k=1024^3 (D=8) with a 768^2 direction grid, 16 views of 800x800, 192 samples."""
+    return scale(seed, k=1024, l=768, n_samples=192, n_cams=16)
+
+
+def fill_position_grid_device(scene: Scene, k: int, sigma_dev, uvw_dev, sigma_host=None, nz: int = 16,
+                              nthreads: int | None = None):
+    """fill_position_grid for grids too large for host memory: z-slabs of nz are generated into a pinned
+    host buffer and copied into the device tensors sigma_dev [k^3] and uvw_dev [k^3 * 3D] (float32).
+    The sigma plane is also kept in sigma_host (float32 [k, k, k]) when given."""
+    import torch
+    nch = 3 * scene.D
+    plane = k * k
+    bufs = [(torch.empty(nz * plane, dtype=torch.float32, pin_memory=True),
+             torch.empty(nz * plane * nch, dtype=torch.float32, pin_memory=True)) for _ in range(2)]
+    done = [None, None]
+    stream = torch.cuda.current_stream(sigma_dev.device)
+    for i, z0 in enumerate(range(0, k, nz)):
+        n = min(nz, k - z0)
+        bs, bu = bufs[i & 1]
+        if done[i & 1] is not None:
+            done[i & 1].synchronize()  # the copy out of this buffer has finished
+        fill_position_grid(scene, k, z0, n, nthreads, sigma_out=bs.numpy()[: n * plane].reshape(n, k, k),
+                           uvw_out=bu.numpy()[: n * plane * nch].reshape(n, k, k, nch))
+        if sigma_host is not None:
+            sigma_host.reshape(k, k, k)[z0:z0 + n] = bs.numpy()[: n * plane].reshape(n, k, k)
+        sigma_dev[z0 * plane:(z0 + n) * plane].copy_(bs[: n * plane], non_blocking=True)
+        uvw_dev[z0 * plane * nch:(z0 + n) * plane * nch].copy_(bu[: n * plane * nch], non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        done[i & 1] = ev
+    torch.cuda.synchronize(sigma_dev.device)
+
+
+def cell_records(scene: Scene, k: int, cells: np.ndarray, nthreads: int | None = None) -> np.ndarray:
+    """uvw channels (float32 [n, 3D]) of the grid cells with linear index (z*k + y)*k + x, evaluated at
+    the cell centres: the values fill_position_grid stores for those cells."""
+    from concurrent.futures import ThreadPoolExecutor
+    cells = np.asarray(cells, dtype=np.int64).reshape(-1)
+    axes = [grid_axis(k, scene.bmin[a], scene.bmax[a]) for a in range(3)]
+    x, y, z = cells % k, (cells // k) % k, cells // (k * k)
+    pts = np.stack([axes[0][x], axes[1][y], axes[2][z]], axis=1)
+    out = np.empty((cells.size, 3 * scene.D), dtype=np.float32)
+    nthreads = nthreads or max(1, os.cpu_count() or 1)
+    chunks = np.array_split(np.arange(cells.size), max(1, min(nthreads * 4, cells.size)))
+
+    def run(ix):
+        if ix.size:
+            out[ix] = eval_points(scene, pts[ix])[1].astype(np.float32)
+
+    with ThreadPoolExecutor(nthreads) as ex:
+        list(ex.map(run, chunks))
+    return out
+
+
 # ---------------------------------------------------------------- MLP weights (cache-build inputs)
 def bf16_bits(x: np.ndarray) -> np.ndarray:
     """binary32 -> bf16 bit patterns, round to nearest even (finite inputs)."""

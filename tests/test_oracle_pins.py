@@ -383,3 +383,41 @@ def test_mlp_forward_vs_numpy():
     # bf16 rounding mode stays within bf16 error of the exact chain
     hb = oracle.mlp_forward(Ws, bs, x, True)
     assert np.max(np.abs(hb - h)) < 0.05 * np.max(np.abs(h))
+
+
+def test_tabled_field_equals_dense(tiny_workload, tiny_arrays):
+    """The cell-table accessor (dense sigma, uvw only for the cells rays shade) is storage only: it gives
+    the dense FP32 render bit for bit, and asks for exactly the occupied cells that rays reach."""
+    w = tiny_workload
+    sig, uvw, beta = tiny_arrays
+    cam = w.cameras()[0]
+    p = oracle.params_struct(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg)
+    dense = oracle.Cache(w.k, w.D, w.l, sig, uvw, beta)
+    py, px = np.meshgrid(np.arange(w.H, dtype=np.int32), np.arange(w.W, dtype=np.int32), indexing="ij")
+    px, py = px.reshape(-1), py.reshape(-1)
+    ref, ref_st, cells = oracle.render_pixels(dense, cam, p, px, py, want_cells=True)
+    flat_uvw = uvw.reshape(-1, 3 * w.D)
+    asked = []
+
+    def records(c):
+        asked.append(c.copy())
+        return flat_uvw[c]
+
+    got, st, n_cells = oracle.render_pixels_tabled(w.k, w.D, w.l, sig.reshape(-1), beta, records, cam, p, px, py)
+    assert np.array_equal(got, ref) and np.array_equal(st, ref_st)
+    c = cells.reshape(-1)
+    c = c[c >= 0]
+    expect = np.unique(c[sig.reshape(-1)[c] > 0])
+    assert n_cells == expect.size > 0 and np.array_equal(asked[0], expect)
+    # a cell left out of the table is counted, not rendered silently wrong
+    import ctypes
+    drop = expect[1:]
+    rec = np.ascontiguousarray(flat_uvw[drop])
+    t = oracle._Table()
+    sflat = np.ascontiguousarray(sig.reshape(-1))
+    t.sigma, t.n, t.cells, t.rec, t.nch, t.missing = sflat.ctypes.data, drop.size, drop.ctypes.data, \
+        rec.ctypes.data, 3 * w.D, 0
+    fn = ctypes.cast(oracle.lib().orc_table_field, ctypes.c_void_p).value
+    c = oracle.Cache(w.k, w.D, w.l, None, None, beta, field=(fn, ctypes.addressof(t)))
+    oracle.render_pixels(c, cam, p, px, py)
+    assert t.missing > 0
