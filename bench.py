@@ -552,7 +552,7 @@ def run_fnr(args):
         step()
     torch.cuda.synchronize()
     frame_events = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                     for _ in range(w.n_cams)] for _ in range(args.steps)]
+                     for _ in range(w.n_cams)] for _ in range(max(5, args.steps // 4))]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         torch.distributed.barrier()
@@ -560,14 +560,19 @@ def run_fnr(args):
     with ClockSampler(local) as clocks:
         t_start.record(stream)
         for s in range(args.steps):
-            step(frame_events[s])
+            step()
         t_end.record(stream)
         torch.cuda.synchronize()
-        # keep the GPU busy a little longer so the sampler sees it under load
     if world > 1:
         torch.distributed.barrier()
     total_ms = t_start.elapsed_time(t_end)
-    frame_ms = np.array([[a.elapsed_time(b) for a, b in ev] for ev in frame_events]).reshape(-1)
+    # per-launch durations (p50/p99 frame time): a second pass with an event pair around every launch,
+    # which also keeps consecutive launches from overlapping
+    lat_steps = max(5, args.steps // 4)
+    for s in range(lat_steps):
+        step(frame_events[s])
+    torch.cuda.synchronize()
+    frame_ms = np.array([[a.elapsed_time(b) for a, b in ev] for ev in frame_events[:lat_steps]]).reshape(-1)
     total_ms = reduce_max(total_ms, world, dev)
     value = job_rate(args.steps * w.n_cams * npix, world, total_ms)
 
@@ -590,9 +595,47 @@ def run_fnr(args):
     e2e_ms = e0.elapsed_time(e1)
     e2e_value = e2e_steps * w.n_cams * npix * world / (e2e_ms * 1e-3) / 1e6
 
+    # empty-space skipping (FNR_RENDER_SKIP_EMPTY): same views, density lookups only in occupied bricks
+    params_skip = fnr.make_params(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg, skip_empty=True)
+    rgba_skip = torch.empty_like(rgba)
+    stats_skip = torch.empty_like(stats)
+    for i in range(w.n_cams):
+        fnr.fnr_render(ctx, cache, [fcams[i]], params_skip, rgba_skip[i], stats_skip[i], stream=stream)
+    fnr.fnr_render(ctx, cache, fcams[:1], params, rgba[0], None, stream=stream)
+    torch.cuda.synchronize()
+    skip_identical = bool(torch.equal(rgba_skip[0], rgba[0]))
+    st_skip = stats_skip.cpu().numpy().reshape(w.n_cams, w.H, w.W, 4)
+    occ_bytes = (((w.k + 7) // 8) ** 3 + 7) // 8
+    alg_skip = float(np.mean([algorithmic_bytes(st_skip[i], w.D, 4, 4, 4) for i in range(w.n_cams)])) + occ_bytes
+    sk_steps = max(5, args.steps // 4)
+    for _ in range(3):
+        for i in range(w.n_cams):
+            fnr.fnr_render(ctx, cache, [fcams[i]], params_skip, rgba_skip[i], None, stream=stream)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for s_ in range(sk_steps):
+        for i in range(w.n_cams):
+            fnr.fnr_render(ctx, cache, [fcams[i]], params_skip, rgba_skip[i], None, stream=stream)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    sk_launch_ms = k0.elapsed_time(k1) / (sk_steps * w.n_cams)
+    del rgba_skip, stats_skip
+
+    # the same 8 views in one launch (fnr_render takes several cameras): no per-launch tail
+    for _ in range(3):
+        fnr.fnr_render(ctx, cache, fcams, params, rgba.view(-1), None, stream=stream)
+    mv_steps = max(5, args.steps // 4)
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(mv_steps):
+        fnr.fnr_render(ctx, cache, fcams, params, rgba.view(-1), None, stream=stream)
+    m1.record(stream)
+    torch.cuda.synchronize()
+    mv_ms = m0.elapsed_time(m1) / mv_steps
+
     if rank == 0:
         peaks, peak_kind = measured_peaks()
-        launch_ms = float(np.mean(frame_ms))
+        launch_ms = total_ms / (args.steps * w.n_cams)  # per launch inside the timed region (back to back)
         achieved = alg_per_launch / (launch_ms * 1e-3) / 1e9
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -609,7 +652,22 @@ def run_fnr(args):
                          "peak": float(peaks["hbm_gbs"]), "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]),
                          "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                          "algorithmic_bytes_per_launch": alg_per_launch, "launch_ms": launch_ms,
+                         "launch_ms_isolated": float(np.mean(frame_ms)),
+                         "timing": "launch_ms = timed region / launches (consecutive launches overlap through "
+                                   "programmatic dependent launch); launch_ms_isolated = mean of event pairs "
+                                   "around single launches",
                          "traffic": None},
+            "skip_empty": {
+                "mrays_per_s": npix / (sk_launch_ms * 1e-3) / 1e6, "launch_ms": sk_launch_ms,
+                "image_bit_identical_to_plain": skip_identical, "occupancy_brick": 8,
+                "lookups_per_ray": float(st_skip[..., 1].mean()), "plain_lookups_per_ray": float(st_all[..., 1].mean()),
+                "roofline": {"bound": "hbm", "achieved": alg_skip / (sk_launch_ms * 1e-3) / 1e9,
+                             "frac": alg_skip / (sk_launch_ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"]),
+                             "algorithmic_bytes_per_launch": alg_skip,
+                             "bytes": "densities looked up + records of occupied samples + beta + RGBA + brick bits"}},
+            "all_views_one_launch": {
+                "mrays_per_s": w.n_cams * npix / (mv_ms * 1e-3) / 1e6, "launch_ms": mv_ms,
+                "roofline_frac": alg_per_launch * w.n_cams / (mv_ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"])},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": w.n_cams * 72,
                     "d2h_bytes_per_step": w.n_cams * npix * 16},
             "clocks": clocks.summary(),

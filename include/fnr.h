@@ -128,7 +128,9 @@ typedef struct {
     int32_t l;             /* direction bins per angle, 2..FNR_MAX_L */
     int32_t pos_precision; /* storage of sigma and (u, v, w): FNR_PREC_* */
     int32_t dir_precision; /* storage of beta: FNR_PREC_FP32 or FNR_PREC_FP16 */
-    int32_t reserved0;
+    int32_t occupancy_brick; /* cells per side of an occupancy brick (FNR_RENDER_SKIP_EMPTY):
+                                a power of two 1..256, or 0 = the smallest power of two >= 2
+                                with ceil(k / B) <= 64 (8 at k = 512, 16 at k = 1024) */
     float bmin[3], bmax[3]; /* bounding box V, bmax > bmin on every axis */
 } fnr_cache_desc;
 
@@ -194,8 +196,13 @@ typedef struct {
     const float *scales_dev;   /* FP8: [1 + 3D] (sigma first), else NULL */
     const float *cos_theta_dev;/* [l] binary32(cos(j pi / l)); entry 0 = 1 */
     const float *phi_key_dev;  /* [l] azimuth-key boundaries; entry 0 = 0 */
+    const uint32_t *occupancy_dev; /* brick occupancy bits: with B = occupancy_brick and
+                                      nb = ceil(k / B), brick (bx, by, bz) holds the cells
+                                      [bx B, bx B + B) x ... clipped to the grid; its index is
+                                      b = (bz nb + by) nb + bx and bit (b & 31) of word b >> 5 is
+                                      set iff one of its stored densities is > 0 */
     int32_t record_stride;     /* bytes between (u, v, w) records */
-    int32_t reserved0;
+    int32_t occupancy_brick;   /* B */
     uint64_t footprint;        /* device bytes */
 } fnr_cache_layout;
 FNR_API fnr_status fnr_cache_get_layout(const fnr_cache *cache, fnr_cache_layout *out);
@@ -213,11 +220,24 @@ typedef struct {
     float t_thr;           /* termination transmittance; <= 0 disables */
     float bg[3];           /* background colour */
     int32_t activation;    /* FNR_ACT_* */
+    uint32_t flags;        /* FNR_RENDER_* bits */
+    int32_t reserved;      /* must be 0 */
 } fnr_render_params;
+
+/* Empty-space skipping (the paper renders with its collision mesh so that
+ * empty space costs no queries, Section 4 and supplementary "Meshing &
+ * Rendering"; here with the cache's brick occupancy bits instead of a mesh):
+ * a sample whose brick has no stored density > 0 is known to have sigma = 0,
+ * so its density is not looked up. The samples stay the N uniform ones, so
+ * RGBA, n_steps, n_occupied and dir_cell equal the plain render's bit for bit;
+ * n_lookups counts only the density lookups made (in-box samples in occupied
+ * bricks, up to termination). */
+#define FNR_RENDER_SKIP_EMPTY 1u
 
 typedef struct {
     int32_t n_steps;    /* samples visited (i + 1 of the terminating sample, else N) */
-    int32_t n_lookups;  /* visited samples inside the cache box */
+    int32_t n_lookups;  /* visited samples inside the cache box (with FNR_RENDER_SKIP_EMPTY:
+                           those in occupied bricks) */
     int32_t n_occupied; /* visited samples with sigma > 0 */
     int32_t dir_cell;   /* i_theta * l + i_phi */
 } fnr_ray_stats;
@@ -313,7 +333,8 @@ FNR_API fnr_status fnr_wait(fnr_context *ctx, uint64_t ticket, uint32_t timeout_
  * calls whose launches overlap on the GPU race, so keep them on one stream or
  * order them. Errors: INVALID_ARG (more than 32 views: the scratch holds one
  * counter per view; NULL arguments; bad params), UNSUPPORTED (D not in
- * {1,2,3,4,6,8,12,16}), CUDA. */
+ * {1,2,3,4,6,8,12,16}; FNR_RENDER_SKIP_EMPTY, which this entry point does not
+ * render), CUDA. */
 FNR_API fnr_status fnr_render_noalloc(const fnr_cache *cache, const fnr_camera *cams, int32_t n_cams,
                                       const fnr_render_params *params, float *rgba_dev, fnr_ray_stats *stats_dev,
                                       uint32_t *done_words, fnr_stream_t stream);

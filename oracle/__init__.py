@@ -30,7 +30,8 @@ class _Cache(ctypes.Structure):
                 ("bmin", ctypes.c_float * 3), ("bmax", ctypes.c_float * 3),
                 ("pos_prec", ctypes.c_int32), ("dir_prec", ctypes.c_int32),
                 ("sigma", ctypes.c_void_p), ("uvw", ctypes.c_void_p), ("beta", ctypes.c_void_p),
-                ("scales", ctypes.c_void_p), ("field", ctypes.c_void_p), ("field_user", ctypes.c_void_p)]
+                ("scales", ctypes.c_void_p), ("field", ctypes.c_void_p), ("field_user", ctypes.c_void_p),
+                ("occ", ctypes.c_void_p), ("occ_brick", ctypes.c_int32)]
 
 
 class _Camera(ctypes.Structure):
@@ -40,7 +41,8 @@ class _Camera(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("t_near", ctypes.c_float), ("t_far", ctypes.c_float),
-                ("t_thr", ctypes.c_float), ("bg", ctypes.c_float * 3), ("act", ctypes.c_int32)]
+                ("t_thr", ctypes.c_float), ("bg", ctypes.c_float * 3), ("act", ctypes.c_int32),
+                ("skip_empty", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -139,7 +141,41 @@ class Cache:
             fn, user = field
             s.field = ctypes.cast(fn, ctypes.c_void_p).value
             s.field_user = user
+        self.occ = None
         self._s = s
+
+    def set_occupancy(self, brick: int, positive: np.ndarray | None = None):
+        """Brick occupancy for skip_empty renders: from the stored densities (positive_density), or from a
+        given boolean [k^3] array of "sigma > 0" (e.g. for a tabled render)."""
+        if positive is None:
+            positive = positive_density(self)
+        self.occ = brick_occupancy(self.k, int(brick), positive)
+        self._s.occ = self.occ.ctypes.data
+        self._s.occ_brick = int(brick)
+        return self
+
+
+def positive_density(cache: "Cache") -> np.ndarray:
+    """bool [k^3]: the stored density, dequantised as the oracle reads it, is > 0."""
+    s = cache.sigma
+    if cache.pos_prec == FP16:
+        h = s.view(np.uint16)
+        return ((h & 0x8000) == 0) & ((h & 0x7FFF) != 0) & ((h & 0x7FFF) <= 0x7C00)
+    if cache.pos_prec == FP8:
+        table = e4m3_decode(np.arange(256)).astype(np.float32)
+        vals = table[s.view(np.uint8)] * np.float32(cache.scales[0])  # binary32 product
+        return vals > 0.0
+    return s.view(np.float32) > 0.0
+
+
+def brick_occupancy(k: int, B: int, positive: np.ndarray) -> np.ndarray:
+    """uint8 [nb^3], nb = ceil(k / B): brick (bz, by, bx) -- the cells [bx B, bx B + B) x [by B, ...) x
+    [bz B, ...) clipped to the grid -- is 1 iff one of its cells has sigma > 0. Index (bz nb + by) nb + bx."""
+    nb = (k + B - 1) // B
+    pos = np.asarray(positive, dtype=bool).reshape(k, k, k)
+    pad = np.zeros((nb * B,) * 3, dtype=bool)
+    pad[:k, :k, :k] = pos
+    return np.ascontiguousarray(pad.reshape(nb, B, nb, B, nb, B).any(axis=(1, 3, 5)).astype(np.uint8).reshape(-1))
 
 
 def camera_struct(cam: dict) -> _Camera:
@@ -150,11 +186,13 @@ def camera_struct(cam: dict) -> _Camera:
     return c
 
 
-def params_struct(N, t_near=2.0, t_far=6.0, t_thr=1e-4, bg=(1.0, 1.0, 1.0), act=ACT_SIGMOID) -> _Params:
+def params_struct(N, t_near=2.0, t_far=6.0, t_thr=1e-4, bg=(1.0, 1.0, 1.0), act=ACT_SIGMOID,
+                  skip_empty=False) -> _Params:
     p = _Params()
     p.N, p.t_near, p.t_far, p.t_thr = int(N), float(t_near), float(t_far), float(t_thr)
     p.bg[:] = [float(v) for v in bg]
     p.act = int(act)
+    p.skip_empty = 1 if skip_empty else 0
     return p
 
 

@@ -54,6 +54,9 @@ typedef struct {
     const float *scales;  /* FP8 only: [1 + 3D] per-channel scales (sigma first) */
     orc_field_fn field;   /* optional: FP64 cell accessor that replaces sigma/uvw */
     void *field_user;
+    const uint8_t *occ;   /* optional: [nb^3] brick occupancy (nb = ceil(k / occ_brick)), brick
+                             (bz nb + by) nb + bx nonzero iff one of its cells has sigma > 0 */
+    int32_t occ_brick;    /* cells per brick side */
 } orc_cache;
 
 typedef struct {
@@ -67,6 +70,7 @@ typedef struct {
     float t_near, t_far, t_thr;
     float bg[3];
     int32_t act;
+    int32_t skip_empty; /* nonzero: samples in bricks without density are not looked up */
 } orc_params;
 
 /* ------------------------------------------------------------ number formats */
@@ -374,8 +378,16 @@ static void render_ray(const ray_ctx *X, int32_t px, int32_t py, double *rgba, i
             if (cells) cells[i] = -1;
             continue;
         }
-        int64_t cell = ((int64_t)floorf(g[2]) * k + (int64_t)floorf(g[1])) * k + (int64_t)floorf(g[0]);
+        const int64_t ix = (int64_t)floorf(g[0]), iy = (int64_t)floorf(g[1]), iz = (int64_t)floorf(g[2]);
+        int64_t cell = (iz * k + iy) * k + ix;
         if (cells) cells[i] = (int32_t)cell;
+        if (p->skip_empty) {
+            /* Empty-space skipping (Section 4, supplementary "Meshing & Rendering"):
+             * a brick with no density holds only sigma = 0, so its samples are
+             * known to be empty without a lookup. */
+            const int64_t B = c->occ_brick, nb = (k + B - 1) / B;
+            if (!c->occ[((iz / B) * nb + iy / B) * nb + ix / B]) continue;
+        }
         n_look += 1;
         double sig = cache_sigma(c, cell);
         if (!(sig > 0.0)) continue;
@@ -436,6 +448,7 @@ int orc_render_pixels(const orc_cache *c, const orc_camera *cam, const orc_param
                       const int32_t *px, const int32_t *py, double *rgba, int32_t *stats, int32_t *cells,
                       int nthreads) {
     if (c->k <= 0 || c->D < 1 || c->D > 16 || c->l < 1 || p->N < 1 || nthreads < 1) return -1;
+    if (p->skip_empty && (!c->occ || c->occ_brick < 1)) return -1;
     float *tab = (float *)malloc(sizeof(float) * (size_t)c->l * 2);
     if (!tab) return -1;
     dir_tables(c->l, tab, tab + c->l);

@@ -30,6 +30,7 @@ FNR_PREC_FP16 = 1
 FNR_PREC_FP8_E4M3 = 2
 FNR_ACT_SIGMOID = 0
 FNR_ACT_IDENTITY = 1
+FNR_RENDER_SKIP_EMPTY = 1
 FNR_SRC_ARRAYS = 1
 FNR_SRC_MLP = 2
 FNR_LOC_HOST = 0
@@ -47,8 +48,8 @@ class FnrError(RuntimeError):
 
 class fnr_cache_desc(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("D", ctypes.c_int32), ("l", ctypes.c_int32),
-                ("pos_precision", ctypes.c_int32), ("dir_precision", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("bmin", ctypes.c_float * 3), ("bmax", ctypes.c_float * 3)]
+                ("pos_precision", ctypes.c_int32), ("dir_precision", ctypes.c_int32),
+                ("occupancy_brick", ctypes.c_int32), ("bmin", ctypes.c_float * 3), ("bmax", ctypes.c_float * 3)]
 
 
 class fnr_mlp(ctypes.Structure):
@@ -65,8 +66,8 @@ class fnr_cache_source(ctypes.Structure):
 class fnr_cache_layout(ctypes.Structure):
     _fields_ = [("sigma_dev", ctypes.c_void_p), ("uvw_dev", ctypes.c_void_p), ("beta_dev", ctypes.c_void_p),
                 ("scales_dev", ctypes.c_void_p), ("cos_theta_dev", ctypes.c_void_p),
-                ("phi_key_dev", ctypes.c_void_p), ("record_stride", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("footprint", ctypes.c_uint64)]
+                ("phi_key_dev", ctypes.c_void_p), ("occupancy_dev", ctypes.c_void_p),
+                ("record_stride", ctypes.c_int32), ("occupancy_brick", ctypes.c_int32), ("footprint", ctypes.c_uint64)]
 
 
 class fnr_camera(ctypes.Structure):
@@ -77,7 +78,8 @@ class fnr_camera(ctypes.Structure):
 
 class fnr_render_params(ctypes.Structure):
     _fields_ = [("n_samples", ctypes.c_int32), ("t_near", ctypes.c_float), ("t_far", ctypes.c_float),
-                ("t_thr", ctypes.c_float), ("bg", ctypes.c_float * 3), ("activation", ctypes.c_int32)]
+                ("t_thr", ctypes.c_float), ("bg", ctypes.c_float * 3), ("activation", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
 
 
 class fnr_ray_stats(ctypes.Structure):
@@ -172,10 +174,11 @@ def fnr_context_used_bytes(ctx: int) -> int:
 
 
 def make_desc(k, D, l, pos_precision=FNR_PREC_FP32, dir_precision=FNR_PREC_FP32, bmin=(-1.5, -1.5, -1.5),
-              bmax=(1.5, 1.5, 1.5)) -> fnr_cache_desc:
+              bmax=(1.5, 1.5, 1.5), occupancy_brick=0) -> fnr_cache_desc:
     d = fnr_cache_desc()
     d.k, d.D, d.l = k, D, l
     d.pos_precision, d.dir_precision = pos_precision, dir_precision
+    d.occupancy_brick = int(occupancy_brick)
     d.bmin[:] = [float(v) for v in bmin]
     d.bmax[:] = [float(v) for v in bmax]
     return d
@@ -261,11 +264,12 @@ def make_camera(cam: dict) -> fnr_camera:
 
 
 def make_params(n_samples, t_near=2.0, t_far=6.0, t_thr=1e-4, bg=(1.0, 1.0, 1.0),
-                activation=FNR_ACT_SIGMOID) -> fnr_render_params:
+                activation=FNR_ACT_SIGMOID, skip_empty=False) -> fnr_render_params:
     p = fnr_render_params()
     p.n_samples, p.t_near, p.t_far, p.t_thr = int(n_samples), float(t_near), float(t_far), float(t_thr)
     p.bg[:] = [float(v) for v in bg]
     p.activation = int(activation)
+    p.flags = FNR_RENDER_SKIP_EMPTY if skip_empty else 0
     return p
 
 

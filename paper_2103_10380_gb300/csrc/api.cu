@@ -41,9 +41,27 @@ int rec_stride_bytes(int prec, int D) {
 static uint64_t align256(uint64_t v) { return (v + 255u) & ~uint64_t(255u); }
 
 struct Layout {
-    uint64_t off_sigma, off_uvw, off_beta, off_ct, off_qp, off_scales, total;
+    uint64_t off_sigma, off_uvw, off_beta, off_ct, off_qp, off_scales, off_occ, total;
     int rec_stride;
 };
+
+// Brick side of the occupancy bits: the descriptor's, or the smallest power of
+// two >= 2 with ceil(k / B) <= 64 (the bits then fit in 32 KB, which stays in L1).
+int occupancy_shift(const fnr_cache_desc *d) {
+    if (d->occupancy_brick > 0) {
+        int sh = 0;
+        while ((1 << sh) < d->occupancy_brick) ++sh;
+        return sh;
+    }
+    int sh = 1;
+    while ((d->k + (1 << sh) - 1) >> sh > 64) ++sh;
+    return sh;
+}
+
+uint64_t occupancy_words(const fnr_cache_desc *d) {
+    const uint64_t nb = uint64_t((d->k + (1 << occupancy_shift(d)) - 1) >> occupancy_shift(d));
+    return (nb * nb * nb + 31u) / 32u;
+}
 
 static bool desc_valid(const fnr_cache_desc *d) {
     if (!d) return false;
@@ -52,6 +70,8 @@ static bool desc_valid(const fnr_cache_desc *d) {
     if (d->dir_precision != FNR_PREC_FP32 && d->dir_precision != FNR_PREC_FP16) return false;
     for (int a = 0; a < 3; ++a)
         if (!(isfinite(d->bmin[a]) && isfinite(d->bmax[a]) && d->bmax[a] > d->bmin[a])) return false;
+    const int B = d->occupancy_brick;
+    if (B < 0 || B > 256 || (B & (B - 1)) != 0) return false;
     return true;
 }
 
@@ -72,6 +92,8 @@ static Layout layout_of(const fnr_cache_desc *d) {
     off = align256(off + uint64_t(d->l) * 4);
     L.off_scales = off;
     off = align256(off + uint64_t(1 + 3 * d->D) * 4);
+    L.off_occ = off;
+    off = align256(off + occupancy_words(d) * 4);
     L.total = off;
     return L;
 }
@@ -202,6 +224,9 @@ static void fill_view(fnr_cache *c, const Layout &L) {
     v.ct = reinterpret_cast<const float *>(base + L.off_ct);
     v.qp = reinterpret_cast<const float *>(base + L.off_qp);
     v.scales = reinterpret_cast<const float *>(base + L.off_scales);
+    v.occ = reinterpret_cast<const uint32_t *>(base + L.off_occ);
+    v.occ_shift = occupancy_shift(&d);
+    v.occ_dim = (d.k + (1 << v.occ_shift) - 1) >> v.occ_shift;
     for (int a = 0; a < 3; ++a) {
         v.bmin[a] = d.bmin[a];
         v.scale[a] = static_cast<float>(static_cast<double>(d.k) /
@@ -226,6 +251,8 @@ fnr_status make_render_const(const fnr_render_params *p, RenderConst *rc) {
     if (isnan(p->t_thr)) return fail(FNR_ERR_INVALID_ARG, "t_thr is NaN");
     if (p->activation != FNR_ACT_SIGMOID && p->activation != FNR_ACT_IDENTITY)
         return fail(FNR_ERR_INVALID_ARG, "unknown activation %d", p->activation);
+    if ((p->flags & ~FNR_RENDER_SKIP_EMPTY) != 0u) return fail(FNR_ERR_INVALID_ARG, "unknown render flags 0x%x", p->flags);
+    if (p->reserved != 0) return fail(FNR_ERR_INVALID_ARG, "reserved field must be 0");
     rc->N = p->n_samples;
     rc->t_near = p->t_near;
     rc->dt = (p->t_far - p->t_near) / static_cast<float>(p->n_samples);
@@ -238,7 +265,7 @@ fnr_status make_render_const(const fnr_render_params *p, RenderConst *rc) {
         rc->s_thr = v >= 9223372036854775807.0 ? 0x7fffffffffffffffLL : (v < 0.0 ? 0 : static_cast<long long>(v));
     }
     for (int c = 0; c < 3; ++c) rc->bg[c] = p->bg[c];
-    rc->pad = 0;
+    rc->flags = p->flags;
     return FNR_OK;
 }
 
@@ -402,6 +429,14 @@ fnr_status fnr_build_cache(fnr_context *ctx, const fnr_cache_desc *desc, const f
             if (st == FNR_OK) st = run_mlp(src->dir_mlp, 1, c->desc, c->view, ctx->num_sms, s);
         }
     }
+    if (st == FNR_OK) {
+        // brick occupancy bits from the stored densities
+        fill_view(c, L);
+        if ((e = cudaMemsetAsync(base + L.off_occ, 0, occupancy_words(desc) * 4, s)) != cudaSuccess ||
+            (e = launch_occupancy(c->view, reinterpret_cast<uint32_t *>(base + L.off_occ), s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            st = cuda_fail(e, "occupancy bits");
+    }
     if (st != FNR_OK) {
         cudaFree(c->base);
         budget_uncharge(ctx, L.total);
@@ -443,8 +478,9 @@ fnr_status fnr_cache_get_layout(const fnr_cache *c, fnr_cache_layout *out) {
     out->scales_dev = c->desc.pos_precision == FNR_PREC_FP8_E4M3 ? v.scales : nullptr;
     out->cos_theta_dev = v.ct;
     out->phi_key_dev = v.qp;
+    out->occupancy_dev = v.occ;
     out->record_stride = v.rec_stride;
-    out->reserved0 = 0;
+    out->occupancy_brick = 1 << v.occ_shift;
     out->footprint = c->footprint;
     return FNR_OK;
 }

@@ -21,6 +21,9 @@ struct CacheView {
     const float *ct;      // [l] cos(theta_j) boundaries
     const float *qp;      // [l] azimuth-key boundaries
     const float *scales;  // FP8: [1 + 3D]
+    const uint32_t *occ;  // brick occupancy bits, brick (bz * occ_dim + by) * occ_dim + bx
+    int32_t occ_shift;    // log2 of the brick side in cells
+    int32_t occ_dim;      // bricks per axis, ceil(k / 2^occ_shift)
     float bmin[3];
     float scale[3];       // binary32(k / (bmax - bmin)) per axis
     float kf;             // (float)k
@@ -37,7 +40,7 @@ struct RenderConst {
     int32_t act;
     long long s_thr;      // termination threshold on the fixed-point optical depth
     float bg[3];
-    int32_t pad;
+    uint32_t flags;       // FNR_RENDER_* bits
 };
 
 // One view inside a launch. Tiles are 8 x 4 pixels, one warp each.
@@ -76,6 +79,10 @@ cudaError_t launch_convert_uvw(const float *in, char *out, int64_t n_cells, int 
 cudaError_t launch_convert_beta(const float *in, void *out, int64_t n, int prec, cudaStream_t s);
 cudaError_t launch_absmax(const float *sigma, const float *uvw, int64_t n_cells, int nch, unsigned *amax_bits,
                           cudaStream_t s);
+// Brick occupancy bits from a stored density plane (words must be zeroed first).
+cudaError_t launch_occupancy(const CacheView &v, uint32_t *words, cudaStream_t s);
+int occupancy_shift(const fnr_cache_desc *d);
+uint64_t occupancy_words(const fnr_cache_desc *d);
 cudaError_t launch_scales_from_absmax(const unsigned *amax_bits, float *scales, int n, cudaStream_t s);
 
 struct Server;

@@ -1,5 +1,6 @@
 // march_device.cuh -- device code of the cached ray march, shared by the
-// plain render kernel (march.cu) and the persistent serving kernel (serve.cu).
+// plain render kernel (march.cu), the serving kernel (serve.cu), the
+// allocation-free kernel (noalloc.cu) and the occupancy build (quant.cu).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -11,14 +12,11 @@ namespace fnr {
 namespace dev {
 
 
-// Tuning knobs (defaults are the measured best; see the design notes):
+// Tuning knobs (defaults are the best measured on GB300):
 //   FNR_UNROLL    density loads issued together per lane
 //   FNR_BLOCK / FNR_MINB  threads per block / minimum resident blocks per SM
-//   FNR_MINB_FP16 / FNR_MINB_FP8  the same for the quantised caches (FP8 keeps
-//                 the per-channel scales folded into beta and needs more registers)
+//   FNR_MINB_FP16 / FNR_MINB_FP8  the same for the quantised caches
 //   FNR_FAST_EXP  1: exponentials of the occupied-sample path via ex2.approx
-//   FNR_QUEUE     1: lanes march density only and queue occupied samples; the
-//                 warp shades 32 queued samples at a time (march_tile_queued)
 #ifndef FNR_UNROLL
 #define FNR_UNROLL 8
 #endif
@@ -36,9 +34,6 @@ namespace dev {
 #endif
 #ifndef FNR_FAST_EXP
 #define FNR_FAST_EXP 1
-#endif
-#ifndef FNR_QUEUE
-#define FNR_QUEUE 1
 #endif
 // FNR_REC_PREFETCH: when an occupied sample is queued, prefetch its record
 // (1: into L2, 2: into L1, 0: no); E4M3 records (24 bytes) measured better without
@@ -129,6 +124,19 @@ __device__ __forceinline__ float load_sigma(const CacheView &c, int cell, float 
     }
 }
 
+// Programmatic dependent launch: a render launch may start while the previous
+// one in its stream finishes (it reads only the cache, which no launch
+// writes); it waits for that launch to complete before its first global write,
+// so outputs keep stream order. Without a programmatic dependency (another
+// kind of launch, a graph node, the first launch) the wait returns at once.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Occupancy bit of an in-grid brick (the bits are small and stay in L1).
+__device__ __forceinline__ unsigned brick_occupied(const CacheView &c, int brick) {
+    return (__ldg(c.occ + (brick >> 5)) >> (brick & 31)) & 1u;
+}
+
 // floor(s * 2^32) for binary32 s, by integer shifts of the significand (no
 // float -> int64 conversion: on this GPU those run on the FP64 pipe).
 // s <= 0 or NaN -> 0; s >= 2^31 -> 2^63 - 1 (saturated).
@@ -173,13 +181,10 @@ __device__ __forceinline__ int dir_cell(const CacheView &c, float dx, float dy, 
     return it * l + ip;
 }
 
-// Per-ray setup shared by both march variants: a1 (ray), a2 (direction cell
-// and beta), and the per-ray affine coefficients of the sample cells with the
-// sample range that can reach the box.
+// Per-ray setup: a1 (ray), a2 (direction cell), and the per-ray affine
+// coefficients of the sample cells with the sample range that can reach the box.
 template <int PREC, int D>
 struct RaySetup {
-    static constexpr int NB = (PREC == FNR_PREC_FP8_E4M3) ? 3 * D : D;
-    float bw[NB];  // beta (FP8: beta_i * scale of channel (ch, i))
     float e[3], f[3];
     int i_lo, i_hi;
     int in_lo, in_hi;  // samples certainly inside the box (the exact test is then redundant)
@@ -199,24 +204,8 @@ struct RaySetup {
         const float dd[3] = {__fdiv_rn(wx, len), __fdiv_rn(wy, len), __fdiv_rn(wz, len)};
         const float oo[3] = {F.c2w[3], F.c2w[7], F.c2w[11]};
 
-        // a2: direction cell and beta
+        // a2: direction cell (beta itself is read by the caller)
         dcell = dir_cell(c, dd[0], dd[1], dd[2]);
-        if constexpr (PREC == FNR_PREC_FP8_E4M3) {
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                float b = c.dir_prec == FNR_PREC_FP16
-                              ? __half2float(__ldg(static_cast<const __half *>(c.beta) + (long long)dcell * D + i))
-                              : __ldg(static_cast<const float *>(c.beta) + (long long)dcell * D + i);
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) bw[ch * D + i] = b * __ldg(c.scales + 1 + ch * D + i);
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < D; ++i)
-                bw[i] = c.dir_prec == FNR_PREC_FP16
-                            ? __half2float(__ldg(static_cast<const __half *>(c.beta) + (long long)dcell * D + i))
-                            : __ldg(static_cast<const float *>(c.beta) + (long long)dcell * D + i);
-        }
         sigma_scale = (PREC == FNR_PREC_FP8_E4M3) ? __ldg(c.scales) : 1.0f;
 
         // a3/a4 per ray: cell coordinates of sample i are g_a = fma(i + 1/2, e_a, f_a)
@@ -296,6 +285,25 @@ struct RaySetup {
         return (iz * c.k + iy) * c.k + ix;
     }
 
+    // The same two with the sample's occupancy brick (meaningful when inside).
+    __device__ __forceinline__ int cell_of_b(const CacheView &c, float fi, int &brick) const {
+        const int ix = __float2int_rd(__fmaf_rn(fi, e[0], f[0]));
+        const int iy = __float2int_rd(__fmaf_rn(fi, e[1], f[1]));
+        const int iz = __float2int_rd(__fmaf_rn(fi, e[2], f[2]));
+        const unsigned int ku = static_cast<unsigned int>(c.k);
+        const bool in = static_cast<unsigned int>(ix) < ku && static_cast<unsigned int>(iy) < ku &&
+                        static_cast<unsigned int>(iz) < ku;
+        brick = ((iz >> c.occ_shift) * c.occ_dim + (iy >> c.occ_shift)) * c.occ_dim + (ix >> c.occ_shift);
+        return in ? (iz * c.k + iy) * c.k + ix : -1;
+    }
+    __device__ __forceinline__ int cell_inside_b(const CacheView &c, float fi, int &brick) const {
+        const int ix = __float2int_rd(__fmaf_rn(fi, e[0], f[0]));
+        const int iy = __float2int_rd(__fmaf_rn(fi, e[1], f[1]));
+        const int iz = __float2int_rd(__fmaf_rn(fi, e[2], f[2]));
+        brick = ((iz >> c.occ_shift) * c.occ_dim + (iy >> c.occ_shift)) * c.occ_dim + (ix >> c.occ_shift);
+        return (iz * c.k + iy) * c.k + ix;
+    }
+
     // a7: Eq. 5 and the activation for one record.
     __device__ __forceinline__ void shade(const Record<PREC, D> &rec, int act, const float *b, float col[3]) const {
         shade_with(rec, act, [&](int ch, int j) { return b[(PREC == FNR_PREC_FP8_E4M3) ? ch * D + j : j]; }, col);
@@ -329,95 +337,6 @@ __device__ __forceinline__ void extinction(float od, float &ext, float &alpha) {
 #endif
 }
 
-template <int PREC, int D>
-__device__ __forceinline__ void march_ray(const CacheView &c, const RenderConst &r, const FrameDesc &F, int px,
-                                          int py) {
-    RaySetup<PREC, D> R;
-    R.init(c, r, F, px, py);
-    const int i_lo = R.i_lo, i_hi = R.i_hi;
-    const float sigma_scale = R.sigma_scale;
-    float T = 1.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
-    long long S = 0;
-    int n_look = 0, n_occ = 0, n_steps = r.N;
-    const long long pix = static_cast<long long>(py) * F.W + px;
-    int32_t *cells_out = F.cells ? F.cells + pix * r.N : nullptr;
-    bool done = false;
-    if (cells_out)
-        for (int i = 0; i < i_lo; ++i) cells_out[i] = -1;
-    float fi = __fadd_rn(static_cast<float>(i_lo), 0.5f);  // i + 0.5, exact in binary32
-
-    // a3-a5 for one group: cells of samples i0 .. i0+U-1 and their density
-    // loads, all issued before any is consumed.
-    auto fill = [&](int i0, int (&cell)[kUnroll], float (&sg)[kUnroll]) {
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            cell[u] = (i0 + u < i_hi) ? R.cell_of(c, fi) : -1;
-            fi = __fadd_rn(fi, 1.0f);
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) sg[u] = cell[u] >= 0 ? load_sigma<PREC>(c, cell[u], sigma_scale) : 0.0f;
-    };
-    // a6-a8 for one group, in sample order, until termination.
-    auto consume = [&](int i0, const int (&cell)[kUnroll], const float (&sg)[kUnroll]) {
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int i = i0 + u;
-            if (i >= i_hi) break;
-            if (cells_out) cells_out[i] = cell[u];
-            if (cell[u] < 0) continue;
-            ++n_look;
-            const float s = sg[u];
-            if (!(s > 0.0f)) continue;
-            ++n_occ;
-            // a6: (u, v, w) record
-            Record<PREC, D> rec;
-            rec.load(c.uvw + static_cast<long long>(cell[u]) * c.rec_stride);
-            // a7: Eq. 5 and the activation
-            float col[3];
-            R.shade(rec, r.act, R.bw, col);
-            // a8: Eq. 1 and exact termination
-            const float od = __fmul_rn(s, r.dt);
-            float ext, alpha;
-            extinction(od, ext, alpha);
-            const float w = T * alpha;
-            Cr = __fmaf_rn(w, col[0], Cr);
-            Cg = __fmaf_rn(w, col[1], Cg);
-            Cb = __fmaf_rn(w, col[2], Cb);
-            T = T * ext;
-            const long long q = fixed_depth(s);
-            S = (S > 0x7fffffffffffffffLL - q) ? 0x7fffffffffffffffLL : S + q;
-            if (S >= r.s_thr) {
-                n_steps = i + 1;
-                done = true;
-                break;
-            }
-        }
-    };
-    for (int i0 = i_lo; i0 < i_hi && !done; i0 += kUnroll) {
-        int cell[kUnroll];
-        float sg[kUnroll];
-        fill(i0, cell, sg);
-        consume(i0, cell, sg);
-    }
-    if (cells_out) {
-        if (done)
-            for (int i = n_steps; i < r.N; ++i) cells_out[i] = -2;
-        else
-            for (int i = max(i_hi, i_lo); i < r.N; ++i) cells_out[i] = -1;
-    }
-    // a9: output
-    float4 o;
-    o.x = __fmaf_rn(T, r.bg[0], Cr);
-    o.y = __fmaf_rn(T, r.bg[1], Cg);
-    o.z = __fmaf_rn(T, r.bg[2], Cb);
-    o.w = 1.0f - T;
-    reinterpret_cast<float4 *>(F.rgba)[pix] = o;
-    if (F.stats) {
-        int4 st = make_int4(n_steps, n_look, n_occ, R.dcell);
-        reinterpret_cast<int4 *>(F.stats)[pix] = st;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Queued variant. The transmittance, the weights w_i = T_i alpha_i and the
 // termination step depend on the densities only, so each lane marches its ray
@@ -438,7 +357,10 @@ struct WarpQueue {
     unsigned int own_mask[32];
 };
 
-template <int PREC, int D>
+// SKIP (FNR_RENDER_SKIP_EMPTY): a sample in a brick without stored density is
+// known to be empty, so only samples in occupied bricks load their density; the
+// lookup counter counts those loads. Everything else is unchanged.
+template <int PREC, int D, bool SKIP>
 __device__ __forceinline__ void march_tile_queued(const CacheView &c, const RenderConst &r, const FrameDesc &F,
                                                   int px, int py, bool active, WarpQueue<D> &q) {
     constexpr unsigned FULL = 0xffffffffu;
@@ -466,6 +388,7 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
     int n_look = 0, n_occ = 0, n_steps = r.N;
     const long long pix = active ? static_cast<long long>(py) * F.W + px : 0;
     int32_t *cells_out = (active && F.cells) ? F.cells + pix * r.N : nullptr;
+    if (F.cells) wait_prior_grid();  // per-sample cells are written while marching
     bool done = !active;
     if (cells_out)
         for (int i = 0; i < R.i_lo; ++i) cells_out[i] = -1;
@@ -529,7 +452,33 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
         // Groups certainly inside the box for every lane still marching take the
         // path without per-sample range tests (warp-uniform choice).
         const bool inside = done || (i0 >= R.in_lo && i0 + kUnroll <= R.in_hi);
-        if (__all_sync(FULL, inside)) {
+        if constexpr (SKIP) {
+            // density lookups only in occupied bricks: in_m = the lookups made
+            if (__all_sync(FULL, inside)) {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    int br;
+                    cell[u] = R.cell_inside_b(c, fi, br);
+                    in_m |= (!done ? brick_occupied(c, br) : 0u) << u;
+                    fi = __fadd_rn(fi, 1.0f);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    int br = 0;
+                    cell[u] = ((vis >> u) & 1u) ? R.cell_of_b(c, fi, br) : -1;
+                    in_m |= (cell[u] >= 0 ? brick_occupied(c, br) : 0u) << u;
+                    fi = __fadd_rn(fi, 1.0f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                sg[u] = ((in_m >> u) & 1u) ? load_sigma<PREC>(c, cell[u], R.sigma_scale) : 0.0f;
+            if constexpr (!kMaxTest) {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) occ_m |= (sg[u] > 0.0f ? 1u : 0u) << u;
+            }
+        } else if (__all_sync(FULL, inside)) {
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
                 cell[u] = R.cell_inside(c, fi);
@@ -641,6 +590,7 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
         __syncwarp();
         flush(0, qn);
     }
+    wait_prior_grid();
     if (!active) return;
     if (cells_out) {
         if (done)

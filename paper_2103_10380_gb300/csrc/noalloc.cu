@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
         const int lt = t - F.tile_begin;
         const int ty = lt / F.tiles_x, tx = lt - ty * F.tiles_x;
         const int px = tx * kTileW + (lane & (kTileW - 1)), py = ty * kTileH + lane / kTileW;
-        dev::march_tile_queued<PREC, D>(A.c, A.r, F, px, py, px < F.W && py < F.H, queues[threadIdx.x >> 5]);
+        dev::march_tile_queued<PREC, D, false>(A.c, A.r, F, px, py, px < F.W && py < F.H, queues[threadIdx.x >> 5]);
         __syncwarp();
         if (lane == 0) {
             __threadfence();
@@ -127,6 +127,8 @@ extern "C" fnr_status fnr_render_noalloc(const fnr_cache *cache, const fnr_camer
     RenderConst rc;
     fnr_status st = make_render_const(params, &rc);
     if (st != FNR_OK) return st;
+    if (rc.flags & FNR_RENDER_SKIP_EMPTY)
+        return fail(FNR_ERR_UNSUPPORTED, "fnr_render_noalloc renders the plain path only (no FNR_RENDER_SKIP_EMPTY)");
     for (int i = 0; i < n_cams; ++i)
         if ((st = check_camera(&cams[i])) != FNR_OK) return st;
     const int prec = cache->desc.pos_precision, D = cache->desc.D;

@@ -6,10 +6,14 @@
 // saturated to +-448, scale_c = absmax_c / 448 (binary32 division; 1 for an
 // all-zero channel). The (u, v, w) records are padded to rec_stride bytes with
 // zeros so every record starts on a 16-byte (FP8: 8-byte) boundary.
+// The brick occupancy bits are derived from the stored densities with the
+// march's own dequantisation, so "brick empty" means exactly that every
+// density the march could load there is 0.
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include "fnr_internal.h"
+#include "march_device.cuh"
 
 namespace fnr {
 
@@ -95,7 +99,35 @@ __global__ void scales_kernel(const unsigned *__restrict__ amax_bits, float *__r
     }
 }
 
+template <int PREC>
+__global__ void occupancy_kernel(const CacheView v, uint32_t *__restrict__ words) {
+    const int64_t k = v.k, n = k * k * k;
+    const float sscale = PREC == FNR_PREC_FP8_E4M3 ? v.scales[0] : 1.0f;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int brick = -1;
+        if (dev::load_sigma<PREC>(v, static_cast<int>(i), sscale) > 0.0f) {
+            const int x = static_cast<int>(i % k), y = static_cast<int>((i / k) % k), z = static_cast<int>(i / (k * k));
+            brick = ((z >> v.occ_shift) * v.occ_dim + (y >> v.occ_shift)) * v.occ_dim + (x >> v.occ_shift);
+        }
+        // one atomic per distinct brick among the warp's active lanes
+        const unsigned act = __activemask();
+        const unsigned same = __match_any_sync(act, brick);
+        if (brick >= 0 && (threadIdx.x & 31) == __ffs(same) - 1)
+            atomicOr(words + (brick >> 5), 1u << (brick & 31));
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_occupancy(const CacheView &v, uint32_t *words, cudaStream_t s) {
+    const int64_t n = static_cast<int64_t>(v.k) * v.k * v.k;
+    const unsigned blocks = grid_for(n, 256);
+    if (v.pos_prec == FNR_PREC_FP16) occupancy_kernel<FNR_PREC_FP16><<<blocks, 256, 0, s>>>(v, words);
+    else if (v.pos_prec == FNR_PREC_FP8_E4M3) occupancy_kernel<FNR_PREC_FP8_E4M3><<<blocks, 256, 0, s>>>(v, words);
+    else occupancy_kernel<FNR_PREC_FP32><<<blocks, 256, 0, s>>>(v, words);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_convert_sigma(const float *in, void *out, int64_t n, int prec, const float *scale, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;

@@ -78,7 +78,7 @@ __device__ __forceinline__ int serve_frame_of(const ServeTable *tab, int nf, int
     return lo;
 }
 
-template <int PREC, int D>
+template <int PREC, int D, bool SKIP>
 __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
     serve_kernel(const ServeTable *__restrict__ tab, ServeScratch *scr, volatile uint32_t *done_flags) {
     constexpr int kWarps = FNR_BLOCK / 32;
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
         const int lt = t - tab->tile_begin[f];
         const int ty = lt / sf.f.tiles_x, tx = lt - ty * sf.f.tiles_x;
         const int px = tx * kTileW + (lane & (kTileW - 1)), py = ty * kTileH + lane / kTileW;
-        dev::march_tile_queued<PREC, D>(sf.c, sf.r, sf.f, px, py, px < sf.f.W && py < sf.f.H, queues[warp]);
+        dev::march_tile_queued<PREC, D, SKIP>(sf.c, sf.r, sf.f, px, py, px < sf.f.W && py < sf.f.H, queues[warp]);
     }
     __syncthreads();  // the block's outputs are written
     if (threadIdx.x == 0) {
@@ -123,28 +123,38 @@ __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
 
 using ServeFn = void (*)(const ServeTable *, ServeScratch *, volatile uint32_t *);
 
-template <int PREC>
+template <int PREC, bool SKIP>
 ServeFn serve_fn_p(int D) {
     switch (D) {
-        case 1: return serve_kernel<PREC, 1>;
-        case 2: return serve_kernel<PREC, 2>;
-        case 3: return serve_kernel<PREC, 3>;
-        case 4: return serve_kernel<PREC, 4>;
-        case 6: return serve_kernel<PREC, 6>;
-        case 8: return serve_kernel<PREC, 8>;
-        case 12: return serve_kernel<PREC, 12>;
-        case 16: return serve_kernel<PREC, 16>;
+        case 1: return serve_kernel<PREC, 1, SKIP>;
+        case 2: return serve_kernel<PREC, 2, SKIP>;
+        case 3: return serve_kernel<PREC, 3, SKIP>;
+        case 4: return serve_kernel<PREC, 4, SKIP>;
+        case 6: return serve_kernel<PREC, 6, SKIP>;
+        case 8: return serve_kernel<PREC, 8, SKIP>;
+        case 12: return serve_kernel<PREC, 12, SKIP>;
+        case 16: return serve_kernel<PREC, 16, SKIP>;
         default: return nullptr;
     }
 }
 
-ServeFn serve_fn(int prec, int D) {
+template <bool SKIP>
+ServeFn serve_fn_s(int prec, int D) {
     switch (prec) {
-        case FNR_PREC_FP32: return serve_fn_p<FNR_PREC_FP32>(D);
-        case FNR_PREC_FP16: return serve_fn_p<FNR_PREC_FP16>(D);
-        case FNR_PREC_FP8_E4M3: return serve_fn_p<FNR_PREC_FP8_E4M3>(D);
+        case FNR_PREC_FP32: return serve_fn_p<FNR_PREC_FP32, SKIP>(D);
+        case FNR_PREC_FP16: return serve_fn_p<FNR_PREC_FP16, SKIP>(D);
+        case FNR_PREC_FP8_E4M3: return serve_fn_p<FNR_PREC_FP8_E4M3, SKIP>(D);
         default: return nullptr;
     }
+}
+
+// Kernel key of a batch: requests share a launch when precision, D and the
+// skip flag agree.
+int serve_key(int prec, int D, bool skip) { return (skip ? 128 : 0) + prec * 32 + D; }
+
+ServeFn serve_fn(int key) {
+    const int prec = (key & 127) / 32, D = key % 32;
+    return key & 128 ? serve_fn_s<true>(prec, D) : serve_fn_s<false>(prec, D);
 }
 
 uint64_t now_ns() {
@@ -157,7 +167,7 @@ struct Request {
     fnr_request req;
     RenderConst rc;
     uint64_t bytes = 0;  // charged against the budget while admitted
-    int key = 0;         // prec * 32 + D: one kernel instance per batch
+    int key = 0;         // serve_key(prec, D, skip): one kernel instance per batch
     int64_t rays = 0;
     int32_t tiles = 0;
     uint64_t t_submit = 0, t_admit = 0, t_done = 0;
@@ -270,7 +280,7 @@ struct Server {
     }
 
     fnr_status launch(Slot &s, int key, int total_tiles) {
-        ServeFn fn = serve_fn(key / 32, key % 32);
+        ServeFn fn = serve_fn(key);
         const unsigned grid = unsigned((total_tiles + FNR_BLOCK / 32 - 1) / (FNR_BLOCK / 32));
         cudaError_t e;
         if (cfg.use_graphs) {
@@ -551,9 +561,9 @@ fnr_status fnr_submit(fnr_context *ctx, const fnr_request *req, uint64_t *ticket
     if (st != FNR_OK) return st;
     if ((st = check_camera(&req->camera)) != FNR_OK) return st;
     const int D = req->cache->desc.D;
-    if (!serve_fn(req->cache->desc.pos_precision, D))
+    r.key = serve_key(req->cache->desc.pos_precision, D, (r.rc.flags & FNR_RENDER_SKIP_EMPTY) != 0u);
+    if (!serve_fn(r.key))
         return fail(FNR_ERR_UNSUPPORTED, "served rendering supports D in {1,2,3,4,6,8,12,16}, got %d", D);
-    r.key = req->cache->desc.pos_precision * 32 + D;
     r.rays = int64_t(req->camera.width) * req->camera.height;
     r.tiles = frame_tiles(&req->camera);
     r.bytes = uint64_t(r.rays) * (16u + (req->stats_dev ? 16u : 0u));

@@ -39,12 +39,32 @@ def test_library_exports_every_declared_symbol(fnr):
     assert names <= set(fnr.SIGNATURES), names - set(fnr.SIGNATURES)
 
 
-def test_struct_sizes_match_header(fnr):
+STRUCTS = ("fnr_cache_desc", "fnr_mlp", "fnr_cache_source", "fnr_cache_layout", "fnr_camera", "fnr_render_params",
+           "fnr_ray_stats", "fnr_request", "fnr_result", "fnr_serve_config")
+
+
+def test_struct_layouts_match_header(fnr, tmp_path):
+    """The binding's ctypes structures have the C header's size and field offsets (gcc compiles the
+    header alone: it needs no CUDA header)."""
     import ctypes
-    assert ctypes.sizeof(fnr.fnr_cache_desc) == 48
-    assert ctypes.sizeof(fnr.fnr_camera) == 72
-    assert ctypes.sizeof(fnr.fnr_render_params) == 32
-    assert ctypes.sizeof(fnr.fnr_ray_stats) == 16
+    import subprocess
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fnr.h"', 'int main(void) {']
+    for name in STRUCTS:
+        lines.append(f'    printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in getattr(fnr, name)._fields_:
+            lines.append(f'    printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("    return 0;\n}")
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    for name in STRUCTS:
+        S = getattr(fnr, name)
+        assert int(got[name]) == ctypes.sizeof(S), name
+        for fname, _ in S._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(S, fname).offset, f"{name}.{fname}"
 
 
 def test_cache_bytes_paper_integers(fnr):

@@ -71,7 +71,8 @@ def gpu_render(fnr, ctx, cache, cams, params, with_cells=False, stream=None):
 
 
 def oparams(p):
-    return oracle.params_struct(p.n_samples, p.t_near, p.t_far, p.t_thr, tuple(p.bg), p.activation)
+    return oracle.params_struct(p.n_samples, p.t_near, p.t_far, p.t_thr, tuple(p.bg), p.activation,
+                                skip_empty=bool(p.flags & 1))
 
 
 def compare(got, ref, tol=TOL):
@@ -338,5 +339,72 @@ def test_scale_workload_sampled_parity(fnr, ctx, scale_arrays):
         py = rng.integers(0, w.H, 300).astype(np.int32)
         _, _, r_cells = oracle.render_pixels(oc, cam, oparams(p), px, py, want_cells=True)
         assert np.array_equal(cells[py, px], r_cells)
+    finally:
+        fnr.fnr_cache_free(ctx, cache)
+
+
+def test_scale_workload_skip_empty(fnr, ctx, scale_arrays):
+    """Empty-space skipping at the benchmark's size (k=512^3, 8-cell bricks): the image and every counter
+    but the lookups equal the plain render bit for bit; the lookups and colours of sampled pixels match the
+    oracle's skip mode; the brick bits equal the oracle's."""
+    w, sig, uvw, beta = scale_arrays
+    cache = build(fnr, ctx, w.k, w.D, w.l, sig, uvw, beta)
+    lay = fnr.fnr_cache_get_layout(cache)
+    assert lay.occupancy_brick == 8
+    oc = oracle.Cache(w.k, w.D, w.l, sig, uvw, beta).set_occupancy(8)
+    nb3 = 64 ** 3
+    words = device_bytes(lay.occupancy_dev, nb3 // 8).view(np.uint32)
+    assert np.array_equal(np.unpackbits(words.view(np.uint8), bitorder="little")[:nb3], oc.occ)
+    try:
+        p, ps = fnr.make_params(w.n_samples), fnr.make_params(w.n_samples, skip_empty=True)
+        rng = np.random.default_rng(2)
+        for cam in w.cameras()[:4]:
+            rgba, st, _ = gpu_render(fnr, ctx, cache, [cam], p)[0]
+            rgba_s, st_s, _ = gpu_render(fnr, ctx, cache, [cam], ps)[0]
+            assert np.array_equal(rgba_s, rgba)
+            assert np.array_equal(st_s[..., [0, 2, 3]], st[..., [0, 2, 3]])
+            assert st_s[..., 1].sum() < 0.7 * st[..., 1].sum()
+            px = rng.integers(0, w.W, 1500).astype(np.int32)
+            py = rng.integers(0, w.H, 1500).astype(np.int32)
+            r_rgba, r_st, _ = oracle.render_pixels(oc, cam, oparams(ps), px, py)
+            assert np.array_equal(st_s[py, px], r_st)
+            assert np.max(np.abs(rgba_s[py, px].astype(np.float64) - r_rgba)) <= TOL
+    finally:
+        fnr.fnr_cache_free(ctx, cache)
+
+
+def test_back_to_back_launches_keep_stream_order(fnr, ctx, tiny_workload, tiny_arrays):
+    """Consecutive renders into the same buffers (launches that may overlap through programmatic
+    dependent launch) leave exactly the last render's output, and a torch kernel queued after a render
+    sees its complete output."""
+    import torch
+    w = tiny_workload
+    sig, uvw, beta = tiny_arrays
+    cache = build(fnr, ctx, w.k, w.D, w.l, sig, uvw, beta)
+    try:
+        cams = scenegen.cameras(55, 3, 256, 192)
+        p = fnr.make_params(w.n_samples)
+        n = 256 * 192
+        ref = []
+        for cam in cams:
+            r = torch.zeros(n * 4, device="cuda")
+            st = torch.zeros(n * 4, device="cuda", dtype=torch.int32)
+            fnr.fnr_render(ctx, cache, [cam], p, r, st)
+            torch.cuda.synchronize()
+            ref.append((r.clone(), st.clone()))
+        rgba = torch.zeros(n * 4, device="cuda")
+        stats = torch.zeros(n * 4, device="cuda", dtype=torch.int32)
+        sums = []
+        for i in range(60):
+            fnr.fnr_render(ctx, cache, [cams[i % 3]], p, rgba, stats)
+            sums.append(rgba.sum())  # a torch kernel between renders reads the whole output
+        torch.cuda.synchronize()
+        assert torch.equal(rgba, ref[59 % 3][0]) and torch.equal(stats, ref[59 % 3][1])
+        for i, v in enumerate(sums):
+            assert float(v) == float(ref[i % 3][0].sum())
+        for i in range(61):  # no reader in between: only the order of writes matters
+            fnr.fnr_render(ctx, cache, [cams[i % 3]], p, rgba, stats)
+        torch.cuda.synchronize()
+        assert torch.equal(rgba, ref[60 % 3][0]) and torch.equal(stats, ref[60 % 3][1])
     finally:
         fnr.fnr_cache_free(ctx, cache)

@@ -421,3 +421,45 @@ def test_tabled_field_equals_dense(tiny_workload, tiny_arrays):
     c = oracle.Cache(w.k, w.D, w.l, None, None, beta, field=(fn, ctypes.addressof(t)))
     oracle.render_pixels(c, cam, p, px, py)
     assert t.missing > 0
+
+
+def test_brick_occupancy_brute_force():
+    """Brick occupancy against a per-brick loop over its cells, with a ragged last brick (k % B != 0)."""
+    k, B = 10, 4
+    rng = np.random.default_rng(5)
+    pos = rng.random(k ** 3) < 0.01
+    occ = oracle.brick_occupancy(k, B, pos)
+    nb = 3
+    P = pos.reshape(k, k, k)
+    for bz in range(nb):
+        for by in range(nb):
+            for bx in range(nb):
+                want = any(P[z, y, x] for z in range(bz * B, min(k, bz * B + B))
+                           for y in range(by * B, min(k, by * B + B)) for x in range(bx * B, min(k, bx * B + B)))
+                assert occ[(bz * nb + by) * nb + bx] == int(want)
+
+
+@pytest.mark.parametrize("brick", [1, 2, 4, 8])
+def test_skip_empty_same_image_fewer_lookups(tiny_workload, tiny_arrays, brick):
+    """Skipping samples in empty bricks changes nothing but the lookup count, which equals the number of
+    visited in-box samples (the plain render's per-sample cells) whose brick holds density."""
+    w = tiny_workload
+    sig, uvw, beta = tiny_arrays
+    cam = w.cameras()[0]
+    c = oracle.Cache(w.k, w.D, w.l, sig, uvw, beta).set_occupancy(brick)
+    p = oracle.params_struct(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg)
+    ps = oracle.params_struct(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg, skip_empty=True)
+    ref, st, cells = oracle.render_image(c, cam, p, want_cells=True)
+    got, st2, cells2 = oracle.render_image(c, cam, ps, want_cells=True)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(st[..., [0, 2, 3]], st2[..., [0, 2, 3]]) and np.array_equal(cells, cells2)
+    k, nb = w.k, (w.k + brick - 1) // brick
+    cz, cy, cx = cells // (k * k), (cells // k) % k, cells % k
+    b = ((cz // brick) * nb + cy // brick) * nb + cx // brick
+    occ = oracle.brick_occupancy(k, brick, sig.reshape(-1) > 0)
+    expect = ((cells >= 0) & (occ[np.where(cells >= 0, b, 0)] == 1)).sum(axis=-1)
+    assert np.array_equal(st2[..., 1], expect)
+    assert (st2[..., 1] <= st[..., 1]).all()
+    if brick == 1:  # single-cell bricks: only occupied samples are looked up
+        assert np.array_equal(st2[..., 1], st2[..., 2])
+    assert st2[..., 1].sum() < st[..., 1].sum()
