@@ -118,6 +118,24 @@ def algorithmic_bytes(stats: np.ndarray, D: int, s_sigma: int, s_uvw: int, s_bet
     return n_look * s_sigma + n_occ * 3 * D * s_uvw + rays * (D * s_beta + 16)
 
 
+# DRAM bytes (read + write) of one plain FP32 march launch of the default workload, from one ncu capture
+# (profiles/march_fp32_k512_800x800_traffic.md); reported only while the kernel sources are unchanged.
+MARCH_TRAFFIC = {"sources_sha256": "bbb3c5522a5cb752ab34ca09d3adddca1dfc810b2f6208cb0b4ebc0ada4981b8",
+                 "bytes_per_launch": 334.1e6, "k": 512}
+MARCH_SOURCES = ("march_device.cuh", "march.cu", "fnr_internal.h")
+
+
+def march_traffic(k: int):
+    import hashlib
+    h = hashlib.sha256()
+    for f in MARCH_SOURCES:
+        with open(os.path.join(ROOT, "paper_2103_10380_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != MARCH_TRAFFIC["sources_sha256"] or k != MARCH_TRAFFIC["k"]:
+        return None
+    return MARCH_TRAFFIC["bytes_per_launch"]
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -656,7 +674,7 @@ def run_fnr(args):
                          "timing": "launch_ms = timed region / launches (consecutive launches overlap through "
                                    "programmatic dependent launch); launch_ms_isolated = mean of event pairs "
                                    "around single launches",
-                         "traffic": None},
+                         "traffic": march_traffic(w.k)},
             "skip_empty": {
                 "mrays_per_s": npix / (sk_launch_ms * 1e-3) / 1e6, "launch_ms": sk_launch_ms,
                 "image_bit_identical_to_plain": skip_identical, "occupancy_brick": 8,
