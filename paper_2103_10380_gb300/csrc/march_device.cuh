@@ -308,19 +308,23 @@ struct RaySetup {
     __device__ __forceinline__ void shade(const Record<PREC, D> &rec, int act, const float *b, float col[3]) const {
         shade_with(rec, act, [&](int ch, int j) { return b[(PREC == FNR_PREC_FP8_E4M3) ? ch * D + j : j]; }, col);
     }
-    // the same with beta_j (times the FP8 scale of channel (ch, j)) supplied by beta_of(ch, j)
+    // the same with beta_j (times the FP8 scale of channel (ch, j)) supplied by beta_of(ch, j); the
+    // loops run component-major, but each channel's sum keeps the order j = 0 .. D-1
     template <class BetaOf>
     __device__ __forceinline__ static void shade_with(const Record<PREC, D> &rec, int act, BetaOf beta_of,
                                                       float col[3]) {
+        float x[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) x[ch] = __fmaf_rn(beta_of(ch, j), rec.get(ch * D + j), x[ch]);
+        }
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            float x = 0.0f;
-#pragma unroll
-            for (int j = 0; j < D; ++j) x = __fmaf_rn(beta_of(ch, j), rec.get(ch * D + j), x);
 #if FNR_FAST_EXP
-            col[ch] = act == FNR_ACT_IDENTITY ? x : __fdividef(1.0f, 1.0f + __expf(-x));
+            col[ch] = act == FNR_ACT_IDENTITY ? x[ch] : __fdividef(1.0f, 1.0f + __expf(-x[ch]));
 #else
-            col[ch] = act == FNR_ACT_IDENTITY ? x : 1.0f / (1.0f + expf(-x));
+            col[ch] = act == FNR_ACT_IDENTITY ? x[ch] : 1.0f / (1.0f + expf(-x[ch]));
 #endif
         }
     }
@@ -407,8 +411,13 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
             rec.load(c.uvw + static_cast<long long>(q.cell[e]) * c.rec_stride);
             if constexpr (PREC == FNR_PREC_FP8_E4M3) {
                 // scaled beta formed at its use: keeps 3D products out of registers
+                float bj = 0.0f;
                 RaySetup<PREC, D>::shade_with(
-                    rec, r.act, [&](int ch, int j) { return q.beta[j][own] * __ldg(c.scales + 1 + ch * D + j); },
+                    rec, r.act,
+                    [&](int ch, int j) {
+                        if (ch == 0) bj = q.beta[j][own];  // read once per component
+                        return bj * __ldg(c.scales + 1 + ch * D + j);
+                    },
                     col);
             } else {
                 float b[D];

@@ -2,16 +2,18 @@
 //
 // A scheduler thread admits queued requests into batch slots as slots and
 // HBM budget free up. Each slot runs one launch per batch on its own stream,
-// replaying a captured CUDA graph (table upload, scratch reset, kernel) whose
-// kernel node gets the batch's grid size. Every block marches 4 consecutive
-// 8 x 4 pixel tiles of the batch's requests (one warp each), then adds its
-// finished tiles to each touched request's counter; the block that completes
-// a request writes the batch epoch into that request's host-mapped completion
-// word, so a request completes as soon as its own tiles are done while the
-// rest of its batch -- and batches on the other slots -- keep the GPU busy.
-// (A persistent grid that pops tiles from a counter measured 20-30% slower
-// per frame than letting the hardware schedule a grid sized to the batch.)
-// No device code waits on anything: completion is observed by the host.
+// replaying a captured CUDA graph of one kernel node whose grid size and
+// parameters -- the batch table itself, passed by value as a __grid_constant__
+// kernel parameter, so no upload precedes the kernel -- are set per batch.
+// Every block marches 4 consecutive 8 x 4 pixel tiles of the batch's requests
+// (one warp each), then adds its finished tiles to each touched request's
+// counter; the block that completes a request resets that counter for the
+// slot's next batch and writes the batch epoch into the request's host-mapped
+// completion word, so a request completes as soon as its own tiles are done
+// while the rest of its batch -- and batches on the other slots -- keep the
+// GPU busy. (A persistent grid that pops tiles from a counter measured 20-30%
+// slower per frame than letting the hardware schedule a grid sized to the
+// batch.) No device code waits on anything: completion is observed by the host.
 #include <string.h>
 
 #include <chrono>
@@ -59,20 +61,21 @@ struct ServeTable {
     ServeFrame frames[kMaxBatch];
 };
 
-struct ServeScratch {  // zeroed before every launch (next_tile is unused by the batch-grid kernel)
-    unsigned int next_tile;
-    unsigned int pad[31];
+// Kernel parameters are limited to 32764 bytes; the table travels as one.
+static_assert(sizeof(ServeTable) <= 32764, "the batch table is a kernel parameter");
+
+struct ServeScratch {  // zeroed once; every request's counter returns to 0 when the request completes
     unsigned int done_tiles[kMaxBatch];
 };
 
 namespace {
 
 // Request of batch tile t: the last request whose first tile is <= t.
-__device__ __forceinline__ int serve_frame_of(const ServeTable *tab, int nf, int t) {
+__device__ __forceinline__ int serve_frame_of(const ServeTable &tab, int nf, int t) {
     int lo = 0, hi = nf - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (tab->tile_begin[mid] <= t) lo = mid;
+        if (tab.tile_begin[mid] <= t) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -80,25 +83,19 @@ __device__ __forceinline__ int serve_frame_of(const ServeTable *tab, int nf, int
 
 template <int PREC, int D, bool SKIP>
 __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
-    serve_kernel(const ServeTable *__restrict__ tab, ServeScratch *scr, volatile uint32_t *done_flags) {
+    serve_kernel(const __grid_constant__ ServeTable tab, ServeScratch *scr, volatile uint32_t *done_flags) {
     constexpr int kWarps = FNR_BLOCK / 32;
     __shared__ dev::WarpQueue<D> queues[kWarps];
-    __shared__ ServeFrame frames_s[kWarps];  // each warp's request, copied once
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int total = tab->total_tiles;
-    const int nf = tab->n_frames;
+    const int total = tab.total_tiles;
+    const int nf = tab.n_frames;
     const int base = blockIdx.x * kWarps;
     if (base >= total) return;  // whole block
     const int t = base + warp;
     if (t < total) {
         const int f = serve_frame_of(tab, nf, t);
-        static_assert(sizeof(ServeFrame) % 8 == 0, "copied in 8-byte words");
-        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&tab->frames[f]);
-        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&frames_s[warp]);
-        for (int i = lane; i < int(sizeof(ServeFrame) / 8); i += 32) dst[i] = src[i];
-        __syncwarp();
-        const ServeFrame &sf = frames_s[warp];
-        const int lt = t - tab->tile_begin[f];
+        const ServeFrame &sf = tab.frames[f];
+        const int lt = t - tab.tile_begin[f];
         const int ty = lt / sf.f.tiles_x, tx = lt - ty * sf.f.tiles_x;
         const int px = tx * kTileW + (lane & (kTileW - 1)), py = ty * kTileH + lane / kTileW;
         dev::march_tile_queued<PREC, D, SKIP>(sf.c, sf.r, sf.f, px, py, px < sf.f.W && py < sf.f.H, queues[warp]);
@@ -109,19 +106,20 @@ __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
         const int last = min(base + kWarps, total);
         for (int t0 = base; t0 < last;) {  // the block's tiles, grouped by request
             const int f = serve_frame_of(tab, nf, t0);
-            const int f_end = f + 1 < nf ? tab->tile_begin[f + 1] : total;
+            const int f_end = f + 1 < nf ? tab.tile_begin[f + 1] : total;
             const int t1 = min(last, f_end);
             const unsigned prev = atomicAdd(&scr->done_tiles[f], unsigned(t1 - t0));
-            if (prev + unsigned(t1 - t0) == static_cast<unsigned>(tab->frames[f].n_tiles)) {
+            if (prev + unsigned(t1 - t0) == static_cast<unsigned>(tab.frames[f].n_tiles)) {
+                scr->done_tiles[f] = 0u;  // every other block of this request has counted
                 __threadfence_system();
-                done_flags[f] = tab->epoch;
+                done_flags[f] = tab.epoch;
             }
             t0 = t1;
         }
     }
 }
 
-using ServeFn = void (*)(const ServeTable *, ServeScratch *, volatile uint32_t *);
+using ServeFn = void (*)(const ServeTable, ServeScratch *, volatile uint32_t *);
 
 template <int PREC, bool SKIP>
 ServeFn serve_fn_p(int D) {
@@ -180,8 +178,7 @@ struct Request {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done_ev = nullptr;
-    ServeTable *h_table = nullptr;  // pinned
-    ServeTable *d_table = nullptr;
+    ServeTable *h_table = nullptr;  // pinned; passed to the kernel by value
     ServeScratch *d_scratch = nullptr;
     uint32_t *h_flags = nullptr;  // pinned, mapped
     uint32_t *d_flags = nullptr;
@@ -289,9 +286,7 @@ struct Server {
                 Slot::Graph G;
                 if ((e = cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
                     return cuda_fail(e, "graph capture");
-                cudaMemcpyAsync(s.d_table, s.h_table, sizeof(ServeTable), cudaMemcpyHostToDevice, s.stream);
-                cudaMemsetAsync(s.d_scratch, 0, sizeof(ServeScratch), s.stream);
-                fn<<<1, FNR_BLOCK, 0, s.stream>>>(s.d_table, s.d_scratch, s.d_flags);
+                fn<<<1, FNR_BLOCK, 0, s.stream>>>(*s.h_table, s.d_scratch, s.d_flags);
                 if ((e = cudaStreamEndCapture(s.stream, &G.graph)) != cudaSuccess) return cuda_fail(e, "graph capture");
                 size_t n = 0;
                 cudaGraphGetNodes(G.graph, nullptr, &n);
@@ -309,7 +304,7 @@ struct Server {
                 it = s.graphs.emplace(key, G).first;
             }
             Slot::Graph &G = it->second;
-            void *args[3] = {&s.d_table, &s.d_scratch, &s.d_flags};
+            void *args[3] = {s.h_table, &s.d_scratch, &s.d_flags};  // the table by value
             cudaKernelNodeParams kp = G.params;
             kp.gridDim = dim3(grid);
             kp.kernelParams = args;
@@ -318,11 +313,7 @@ struct Server {
                 return cuda_fail(e, "graph update");
             if ((e = cudaGraphLaunch(G.exec, s.stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
         } else {
-            if ((e = cudaMemcpyAsync(s.d_table, s.h_table, sizeof(ServeTable), cudaMemcpyHostToDevice, s.stream)) !=
-                    cudaSuccess ||
-                (e = cudaMemsetAsync(s.d_scratch, 0, sizeof(ServeScratch), s.stream)) != cudaSuccess)
-                return cuda_fail(e, "batch upload");
-            fn<<<grid, FNR_BLOCK, 0, s.stream>>>(s.d_table, s.d_scratch, s.d_flags);
+            fn<<<grid, FNR_BLOCK, 0, s.stream>>>(*s.h_table, s.d_scratch, s.d_flags);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "serve launch");
         }
         if ((e = cudaEventRecord(s.done_ev, s.stream)) != cudaSuccess) return cuda_fail(e, "event record");
@@ -455,8 +446,9 @@ static fnr_status server_start(fnr_context *ctx, const fnr_serve_config *cfg_in)
             (e = cudaEventCreateWithFlags(&s.done_ev, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaHostAlloc(reinterpret_cast<void **>(&s.h_table), sizeof(ServeTable), cudaHostAllocDefault)) !=
                 cudaSuccess ||
-            (e = cudaMalloc(&s.d_table, sizeof(ServeTable))) != cudaSuccess ||
             (e = cudaMalloc(&s.d_scratch, sizeof(ServeScratch))) != cudaSuccess ||
+            (e = cudaMemsetAsync(s.d_scratch, 0, sizeof(ServeScratch), s.stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s.stream)) != cudaSuccess ||
             (e = cudaHostAlloc(reinterpret_cast<void **>(&s.h_flags), sizeof(uint32_t) * kMaxBatch,
                                cudaHostAllocMapped)) != cudaSuccess ||
             (e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s.d_flags), s.h_flags, 0)) != cudaSuccess) {
@@ -471,7 +463,6 @@ static fnr_status server_start(fnr_context *ctx, const fnr_serve_config *cfg_in)
             if (s.stream) cudaStreamDestroy(s.stream);
             if (s.done_ev) cudaEventDestroy(s.done_ev);
             if (s.h_table) cudaFreeHost(s.h_table);
-            if (s.d_table) cudaFree(s.d_table);
             if (s.d_scratch) cudaFree(s.d_scratch);
             if (s.h_flags) cudaFreeHost(s.h_flags);
         }
@@ -502,7 +493,6 @@ void server_stop(fnr_context *ctx) {
         cudaStreamDestroy(s.stream);
         cudaEventDestroy(s.done_ev);
         cudaFreeHost(s.h_table);
-        cudaFree(s.d_table);
         cudaFree(s.d_scratch);
         cudaFreeHost(s.h_flags);
     }
