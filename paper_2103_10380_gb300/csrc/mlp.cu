@@ -40,23 +40,34 @@ namespace {
 constexpr int kTileM = 128;
 constexpr int kMaxK = 256;
 constexpr int kMaxN = 256;
-constexpr int kChunkK = 32;                          // K columns per weight chunk
-constexpr int kSlots = 4;                            // ring slots
-constexpr int kSlotBytes = kMaxN * kChunkK * 2;      // 16 KB
-constexpr int kPair = 2;                             // tiles in flight per CTA
+constexpr int kChunkK = 64;                          // K columns per weight chunk: one 128-byte swizzle row
+#ifndef FNR_MLP_SLOTS
+#define FNR_MLP_SLOTS 3
+#endif
+#ifndef FNR_MLP_PAIR
+#define FNR_MLP_PAIR 2
+#endif
+#ifndef FNR_MLP_BIAS_SMEM
+#define FNR_MLP_BIAS_SMEM 0
+#endif
+constexpr int kSlots = FNR_MLP_SLOTS;                // ring slots
+constexpr int kSlotBytes = kMaxN * kChunkK * 2;      // 32 KB
+constexpr int kPair = FNR_MLP_PAIR;                  // tiles in flight per CTA
 constexpr int kProducerWarp = 0, kMmaWarp = 1, kFirstEpiWarp = 4, kEpiWarps = 16;
 constexpr int kThreads = (kFirstEpiWarp + kEpiWarps) * 32;
 constexpr int kMaxLayers = 16;
 constexpr int kMaxBias = kMaxLayers * kMaxN;
 constexpr uint32_t kTmemCols = 256 * kPair;                                // one accumulator per tile
-constexpr size_t kSmemA = size_t(kPair) * kTileM * kMaxK * 2;               // 2 x 64 KB activations
-constexpr size_t kSmemRing = size_t(kSlots) * kSlotBytes;                   // 64 KB weights
-constexpr size_t kSmemBias = size_t(kMaxBias) * 4;                          // 16 KB biases
-constexpr size_t kSmemBytes = kSmemA + kSmemRing + kSmemBias + 256;
+constexpr size_t kSmemA = size_t(kPair) * kTileM * kMaxK * 2;               // 64 KB activations per tile
+constexpr size_t kSmemRing = size_t(kSlots) * kSlotBytes;                   // weight chunks
+constexpr size_t kSmemBias = FNR_MLP_BIAS_SMEM ? size_t(kMaxBias) * 4 : 0;  // 16 KB biases (else read via L1)
+constexpr size_t kSmemBars = (size_t(2 * kSlots + 2 * kPair) * 8 + 16 + 127) / 128 * 128;
+constexpr size_t kSmemBytes = kSmemA + kSmemRing + kSmemBias + kSmemBars + 1024;  // + alignment slack
+static_assert(kSmemBytes <= 232448, "shared memory per CTA");
 constexpr long long kWaitLimit = 1LL << 22;                                 // try_wait polls before giving up
 
 struct MlpLayerDev {
-    const __nv_bfloat16 *w;  // chunk-major: chunk c = [Np][kc] in core-matrix layout, chunks of Np*kChunkK elements
+    const __nv_bfloat16 *w;  // chunk-major: chunk c = [Np][64] in the 128-byte swizzled K-major layout
     int K, N;                // padded to multiples of 16
     int bias_off;            // offset of this layer's Np biases in the bias table
 };
@@ -130,15 +141,20 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major, no swizzle, 8x8 core matrices;
-// lbo = byte distance between core matrices along K, sbo = along M / N.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor, K-major with the 128-byte swizzle: rows of
+// 64 bf16 (128 bytes), 8-row atoms of 1024 bytes stacked along M / N
+// (stride 1024), the 16-byte pieces of row r stored at piece index ^ (r & 7).
+// Atoms start on 1024-byte boundaries; a K step of 16 inside the atom row
+// advances the start address by 32 bytes. The leading-dimension offset is
+// unused by this layout (encoded as 1).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     uint64_t d = 0;
     d |= uint64_t((addr >> 4) & 0x3FFFu);
-    d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
-    d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
-    d |= uint64_t(1) << 46;  // descriptor version for this architecture
-    return d;                // base offset 0, swizzle none
+    d |= uint64_t(1) << 16;                 // leading byte offset (unused), 16 bytes
+    d |= uint64_t(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 bytes
+    d |= uint64_t(1) << 46;                 // descriptor version for this architecture
+    d |= uint64_t(2) << 61;                 // swizzle mode: 128 bytes
+    return d;                               // base offset 0
 }
 
 // Instruction descriptor, kind::f16: bf16 A and B (both K-major), fp32 D.
@@ -176,9 +192,11 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
 
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Byte offset of element (row, k) in a K-major core-matrix tile with Kp columns.
-__device__ __forceinline__ uint32_t cm_offset(int row, int k, int Kp) {
-    return uint32_t((row >> 3) * (Kp >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+// Byte offset of element (row, k) of the A tile (kTileM rows) in the 128-byte
+// swizzled K-major layout: 64-column K blocks of kTileM / 8 atoms each.
+__device__ __forceinline__ uint32_t a_offset(int row, int k) {
+    return uint32_t((k >> 6) * (kTileM / 8) * 1024 + (row >> 3) * 1024 + (row & 7) * 128 +
+                    ((((k >> 3) & 7) ^ (row & 7)) << 4) + (k & 7) * 2);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -228,15 +246,16 @@ __device__ __forceinline__ void encode_point(const MlpArgs &A, long long p, int 
         pk.y = pack_bf16(v[2], v[3]);
         pk.z = pack_bf16(v[4], v[5]);
         pk.w = pack_bf16(v[6], v[7]);
-        *reinterpret_cast<uint4 *>(sa + cm_offset(row, g, K0)) = pk;
+        *reinterpret_cast<uint4 *>(sa + a_offset(row, g)) = pk;
     }
 }
 
-__device__ __forceinline__ int n_chunks(int K) { return (K + kChunkK - 1) / kChunkK; }
-__device__ __forceinline__ int chunk_width(int K, int c) { return min(kChunkK, K - c * kChunkK); }
+__device__ __forceinline__ int n_chunks(int K) { return K / kChunkK; }  // K is padded to a multiple of 64
 
 __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant__ MlpArgs A) {
-    extern __shared__ __align__(1024) char smem[];
+    extern __shared__ __align__(1024) char smem_raw[];
+    // the swizzled operand tiles start on 1024-byte boundaries
+    char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     char *sa = smem;  // A tile of slot t at sa + t * kTileM * kMaxK * 2
     char *ring = smem + kSmemA;
     float *sbias = reinterpret_cast<float *>(smem + kSmemA + kSmemRing);
@@ -252,7 +271,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
     auto a_ready = [&](int t) { return bar0 + 8u * uint32_t(2 * kSlots + kPair + t); };
     constexpr uint32_t kATileBytes = uint32_t(kTileM) * kMaxK * 2;
 
-    for (int i = tid; i < A.n_bias; i += kThreads) sbias[i] = A.bias[i];
+    if (FNR_MLP_BIAS_SMEM)
+        for (int i = tid; i < A.n_bias; i += kThreads) sbias[i] = A.bias[i];
     if (tid == 0) {
         for (int s = 0; s < kSlots; ++s) {
             mbar_init(full_bar(s), 1);
@@ -275,12 +295,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    // Tiles go to CTAs in pairs: the CTA's pair r holds tiles (2r) * grid + bid and (2r + 1) * grid + bid;
+    // Tiles go to CTAs in groups of kPair: group r holds tiles (kPair r + t) * grid + bid, t < kPair;
     // a tile past the end is carried as an empty one (no outputs).
     const long long n_tiles = (A.n_points + kTileM - 1) / kTileM;
     const long long G = gridDim.x;
-    auto pair_tile = [&](long long r, int t) { return (2 * r + t) * G + blockIdx.x; };
-    const long long n_pairs = (n_tiles - blockIdx.x + 2 * G - 1) / (2 * G);
+    auto pair_tile = [&](long long r, int t) { return (kPair * r + t) * G + blockIdx.x; };
+    const long long n_pairs = (n_tiles - blockIdx.x + kPair * G - 1) / (kPair * G);
 
     if (warp == kProducerWarp) {
         if (lane == 0) {
@@ -296,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
                             if (round > 0 &&
                                 !mbar_wait(empty_bar(slot), uint32_t((round - 1) & 1), A.err, &abort_flag))
                                 break;
-                            const uint32_t bytes = uint32_t(Ly.N) * uint32_t(chunk_width(Ly.K, c)) * 2u;
+                            const uint32_t bytes = uint32_t(Ly.N) * uint32_t(kChunkK) * 2u;
                             mbar_expect_tx(full_bar(slot), bytes);
                             bulk_g2s(smem_u32(ring) + uint32_t(slot) * kSlotBytes,
                                      reinterpret_cast<const char *>(Ly.w) + size_t(c) * Ly.N * kChunkK * 2, bytes,
@@ -314,7 +334,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
                         if (!mbar_wait(a_ready(t), uint32_t(uses & 1), A.err, &abort_flag)) break;
                         tc_fence_after();
                         const uint32_t idesc = instr_desc(kTileM, Ly.N);
-                        const uint32_t sbo_a = uint32_t(Ly.K >> 3) * 128u;
                         const uint32_t a_base = smem_u32(sa) + uint32_t(t) * kATileBytes;
                         const uint32_t d_tmem = tmem + uint32_t(t * 256);
                         const int nc = n_chunks(Ly.K);
@@ -322,14 +341,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
                             const int slot = int(it % kSlots);
                             if (!mbar_wait(full_bar(slot), uint32_t((it / kSlots) & 1), A.err, &abort_flag)) break;
                             tc_fence_after();
-                            const int kc = chunk_width(Ly.K, c);
-                            const uint32_t sbo_b = uint32_t(kc >> 3) * 128u;
-                            for (int s = 0; s < kc / 16; ++s) {
-                                const uint64_t ad = smem_desc(
-                                    a_base + uint32_t(c) * uint32_t(kChunkK / 8) * 128u + uint32_t(s) * 256u, 128u,
-                                    sbo_a);
-                                const uint64_t bd = smem_desc(
-                                    smem_u32(ring) + uint32_t(slot) * kSlotBytes + uint32_t(s) * 256u, 128u, sbo_b);
+#pragma unroll
+                            for (int s = 0; s < kChunkK / 16; ++s) {
+                                const uint64_t ad = smem_desc_sw128(a_base + uint32_t(c) * (kTileM / 8) * 1024u +
+                                                                    uint32_t(s) * 32u);
+                                const uint64_t bd =
+                                    smem_desc_sw128(smem_u32(ring) + uint32_t(slot) * kSlotBytes + uint32_t(s) * 32u);
                                 umma_bf16(d_tmem, ad, bd, idesc, (c > 0 || s > 0) ? 1u : 0u);
                             }
                             umma_commit(empty_bar(slot));
@@ -358,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
                 const MlpLayerDev &Ly = A.L[li];
                 const int N = Ly.N;
                 const bool last = li + 1 == A.n_layers;
-                const float *bias = sbias + Ly.bias_off;
+                const float *bias = (FNR_MLP_BIAS_SMEM ? sbias : A.bias) + Ly.bias_off;
                 for (int t = 0; t < kPair; ++t) {
                     int ok = 1;
                     if (lane == 0) ok = mbar_wait(acc_full(t), uint32_t(uses & 1), A.err, &abort_flag) ? 1 : 0;
@@ -379,7 +396,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
                         float v[16];
 #pragma unroll
                         for (int u = 0; u < 16; u += 4) {
-                            const float4 b4 = *reinterpret_cast<const float4 *>(bias + c0 + u);
+                            const float4 b4 = FNR_MLP_BIAS_SMEM ? *reinterpret_cast<const float4 *>(bias + c0 + u)
+                                                                : __ldg(reinterpret_cast<const float4 *>(bias + c0 + u));
                             v[u + 0] = __uint_as_float(rr[u + 0]) + b4.x;
                             v[u + 1] = __uint_as_float(rr[u + 1]) + b4.y;
                             v[u + 2] = __uint_as_float(rr[u + 2]) + b4.z;
@@ -393,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
                                 pk.y = pack_bf16(fmaxf(v[u + 2], 0.0f), fmaxf(v[u + 3], 0.0f));
                                 pk.z = pack_bf16(fmaxf(v[u + 4], 0.0f), fmaxf(v[u + 5], 0.0f));
                                 pk.w = pack_bf16(fmaxf(v[u + 6], 0.0f), fmaxf(v[u + 7], 0.0f));
-                                *reinterpret_cast<uint4 *>(sa_t + cm_offset(row, c0 + u, N)) = pk;
+                                *reinterpret_cast<uint4 *>(sa_t + a_offset(row, c0 + u)) = pk;
                             }
                         } else if (valid) {
 #pragma unroll
@@ -429,6 +447,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
                         process(r0, j0);
                         if (two) process(r1, j0 + 4);
                     }
+                    if (!last) {  // K padding of the next layer: columns [N, roundup(N, 64)) are 0
+                        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+                        for (int c8 = N + 8 * g; c8 < ((N + 63) & ~63); c8 += 32)
+                            *reinterpret_cast<uint4 *>(sa_t + a_offset(row, c8)) = z;
+                    }
                     tc_fence_before();
                     if (!last) {
                         fence_proxy_async();
@@ -448,17 +471,18 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
     }
 }
 
-// W [N][K] row-major bf16 bits -> padded, chunk-major core-matrix layout:
-// chunk c holds columns [kChunkK c, kChunkK c + kc) as [Np][kc] K-major core matrices.
+// W [N][K] row-major bf16 bits -> padded, chunk-major 128-byte swizzled layout:
+// chunk c holds columns [64 c, 64 c + 64) as [Np][64] K-major rows of 128
+// bytes, 8-row atoms of 1024 bytes, piece (k / 8) of row n at (k / 8) ^ (n & 7).
 __global__ void relayout_kernel(const uint16_t *__restrict__ w, int N, int K, uint16_t *__restrict__ out, int Np,
                                 int Kp) {
     const int total = Np * Kp;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const int n = e / Kp, k = e - n * Kp;
         const uint16_t v = (n < N && k < K) ? w[size_t(n) * K + k] : uint16_t(0);
-        const int c = k / kChunkK, kk = k - c * kChunkK, kc = min(kChunkK, Kp - c * kChunkK);
-        const size_t off = size_t(c) * Np * kChunkK + size_t(n >> 3) * (kc >> 3) * 64 + size_t(kk >> 3) * 64 +
-                           size_t(n & 7) * 8 + (kk & 7);
+        const int c = k / kChunkK, kk = k - c * kChunkK;
+        const size_t off = size_t(c) * Np * kChunkK + size_t(n >> 3) * 512 + size_t(n & 7) * 64 +
+                           size_t(((kk >> 3) ^ (n & 7)) & 7) * 8 + (kk & 7);
         out[off] = v;
     }
 }
@@ -469,6 +493,7 @@ __global__ void pad_bias_kernel(const float *__restrict__ b, int N, float *__res
 }
 
 int round16(int v) { return (v + 15) / 16 * 16; }
+int round64(int v) { return (v + 63) / 64 * 64; }
 
 }  // namespace
 
@@ -482,7 +507,7 @@ fnr_status check_mlp(const fnr_mlp *m, int n_out_min, const char *name) {
         return fail(FNR_ERR_INVALID_ARG, "%s: dims[0]=%d cannot hold 2*3*%d encoded inputs", name, m->dims[0],
                     m->pe_freqs);
     for (int i = 0; i <= m->n_layers; ++i)
-        if (m->dims[i] < 1 || round16(m->dims[i]) > kMaxK)
+        if (m->dims[i] < 1 || round64(m->dims[i]) > kMaxK)
             return fail(FNR_ERR_UNSUPPORTED, "%s: layer width %d outside [1, %d]", name, m->dims[i], kMaxK);
     if (m->dims[m->n_layers] < n_out_min)
         return fail(FNR_ERR_INVALID_ARG, "%s: %d outputs, need %d", name, m->dims[m->n_layers], n_out_min);
@@ -502,7 +527,7 @@ fnr_status run_mlp(const fnr_mlp *m, int mode, const fnr_cache_desc &d, const Ca
     } wbuf, bbuf, ebuf;
     size_t welems = 0, belems = 0;
     for (int i = 0; i < m->n_layers; ++i) {
-        welems += size_t(round16(m->dims[i + 1])) * round16(m->dims[i]);
+        welems += size_t(round16(m->dims[i + 1])) * round64(m->dims[i]);
         belems += size_t(round16(m->dims[i + 1]));
     }
     cudaError_t e;
@@ -514,7 +539,7 @@ fnr_status run_mlp(const fnr_mlp *m, int mode, const fnr_cache_desc &d, const Ca
     memset(&A, 0, sizeof(A));
     size_t wo = 0, bo = 0;
     for (int i = 0; i < m->n_layers; ++i) {
-        const int K = m->dims[i], N = m->dims[i + 1], Kp = round16(K), Np = round16(N);
+        const int K = m->dims[i], N = m->dims[i + 1], Kp = round64(K), Np = round16(N);
         uint16_t *wd = static_cast<uint16_t *>(wbuf.p) + wo;
         float *bd = static_cast<float *>(bbuf.p) + bo;
         relayout_kernel<<<(Np * Kp + 255) / 256, 256, 0, s>>>(m->weights[i], N, K, wd, Np, Kp);

@@ -174,3 +174,24 @@ def test_render_mlp_built_cache(fnr):
         assert np.max(np.abs(rgba.cpu().numpy().reshape(40, 48, 4) - ref)) <= 1e-5
     finally:
         fnr.fnr_context_destroy(ctx)
+
+
+def test_widths_not_multiple_of_64(fnr):
+    """Hidden widths of 80 and 48: the K padding of the next layer's input (to 64-column blocks) must read
+    as zeros."""
+    k, l, D = 8, 8, 8
+    pos = scenegen.mlp_weights(5, [60, 80, 48, 25], bias_scale=0.3)
+    dirn = scenegen.mlp_weights(6, [24, 40, 8], bias_scale=0.3)
+    ctx = fnr.fnr_context_create(0, 0)
+    try:
+        cache = build(fnr, ctx, k, l, D, pos, dirn)
+        sig, uvw, beta = read_cache(fnr, cache, k, D, l)
+        xyz = oracle.cell_centres(k, np.arange(k ** 3))
+        ref_b = oracle.mlp_eval(as_fp64(pos), xyz, 10, True)
+        got = np.concatenate([sig[:, None], uvw], axis=1)
+        ref = np.concatenate([np.maximum(ref_b[:, :1], 0), ref_b[:, 1:]], axis=1)
+        check_channels(got, ref)
+        dirs = oracle.bin_directions(l, np.arange(l * l))
+        check_channels(beta, oracle.mlp_eval(as_fp64(dirn), dirs, 4, True))
+    finally:
+        fnr.fnr_context_destroy(ctx)
