@@ -5,24 +5,30 @@
 //
 // One CTA per SM walks tiles of 128 grid points with three warp roles:
 //   producer (warp 0): streams every layer's bf16 weights, pre-arranged in
-//     32-wide K chunks of the UMMA K-major no-swizzle layout, through a 4-slot
-//     shared-memory ring by bulk async copy (cp.async.bulk, completion on the
-//     slot's "full" mbarrier), running ahead across layers and tiles;
-//   two tiles are in flight: each has its own A tile and its own tensor-memory
-//     accumulator, so one tile's epilogue runs while the other's MMAs do;
+//     64-column K chunks of the K-major 128-byte swizzled operand layout,
+//     through a 3-slot shared-memory ring by bulk async copy (cp.async.bulk,
+//     completion on the slot's "full" mbarrier), running ahead across layers
+//     and tiles;
+//   two tiles are in flight: each has its own A tile (same swizzled layout)
+//     and its own tensor-memory accumulator, so one tile's epilogue runs while
+//     the other's MMAs do;
 //   MMA issuer (warp 1, one lane): waits for the layer input and each chunk,
-//     issues tcgen05.mma (M=128, N=layer width, bf16 x bf16 -> fp32 in tensor
-//     memory), releases each slot with tcgen05.commit on its "empty" mbarrier
-//     and signals the finished accumulator with one more commit;
+//     issues tcgen05.mma (M=128, N=layer width, K=16 steps, bf16 x bf16 ->
+//     fp32 in tensor memory), releases each slot with tcgen05.commit on its
+//     "empty" mbarrier and signals the finished accumulator with one more commit;
 //   epilogue (warps 4-19, four per 32-lane quarter of tensor memory): encode
 //     the tile's points (gamma(x) = sin / cos(2^j pi x), rounded to bf16) into
 //     the A tile, then per layer read the accumulator (tcgen05.ld), add the
 //     bias, apply ReLU, round to bf16 and write the next layer's A tile -- or,
 //     after the head, write sigma = ReLU(out_0), (u, v, w) = out_1..3D (F_pos)
-//     or beta = out_0..D-1 (F_dir) straight into the cache.
+//     or beta = out_0..D-1 (F_dir) straight into the cache, then encode the
+//     tile's next points while the other tile is still in flight.
 // The next layer's weights load while the epilogue runs. Every mbarrier wait
 // is bounded; a wait that runs out sets the error word and a CTA-wide abort
 // flag, every role leaves its loop, and the tensor memory is freed.
+// Optionally (FNR_MLP_CLUSTER > 1) clusters of CTAs share each weight chunk
+// through multicast bulk copies; measured no faster, so off by default.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -41,6 +47,12 @@ constexpr int kTileM = 128;
 constexpr int kMaxK = 256;
 constexpr int kMaxN = 256;
 constexpr int kChunkK = 64;                          // K columns per weight chunk: one 128-byte swizzle row
+// FNR_MLP_CLUSTER: CTAs per thread-block cluster; each CTA loads 1/n of every
+// weight chunk and multicasts it to the cluster, so the L2 serves each chunk
+// once per cluster instead of once per CTA
+#ifndef FNR_MLP_CLUSTER
+#define FNR_MLP_CLUSTER 1
+#endif
 #ifndef FNR_MLP_SLOTS
 #define FNR_MLP_SLOTS 3
 #endif
@@ -51,9 +63,20 @@ constexpr int kChunkK = 64;                          // K columns per weight chu
 #define FNR_MLP_BIAS_SMEM 0
 #endif
 constexpr int kSlots = FNR_MLP_SLOTS;                // ring slots
+constexpr int kCluster = FNR_MLP_CLUSTER;            // CTAs sharing each weight chunk
 constexpr int kSlotBytes = kMaxN * kChunkK * 2;      // 32 KB
 constexpr int kPair = FNR_MLP_PAIR;                  // tiles in flight per CTA
-constexpr int kProducerWarp = 0, kMmaWarp = 1, kFirstEpiWarp = 4, kEpiWarps = 16;
+#ifndef FNR_MLP_FIRST_EPI
+#define FNR_MLP_FIRST_EPI 4
+#endif
+#ifndef FNR_MLP_LD4
+#define FNR_MLP_LD4 0
+#endif
+#ifndef FNR_MLP_KATTR
+#define FNR_MLP_KATTR __launch_bounds__(kThreads, 1)
+#endif
+// epilogue warp w reads tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31
+constexpr int kProducerWarp = 0, kMmaWarp = 1, kFirstEpiWarp = FNR_MLP_FIRST_EPI, kEpiWarps = 16;
 constexpr int kThreads = (kFirstEpiWarp + kEpiWarps) * 32;
 constexpr int kMaxLayers = 16;
 constexpr int kMaxBias = kMaxLayers * kMaxN;
@@ -135,6 +158,17 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
+// The same, one slice multicast to the CTAs of the cluster in cta_mask (same
+// shared-memory offsets; each destination's mbarrier receives the slice's bytes).
+__device__ __forceinline__ void bulk_g2s_multicast(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
+                                                   uint16_t cta_mask) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar), "h"(cta_mask)
+        : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -179,6 +213,14 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
 
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Commit that arrives on the mbarrier at this offset in every CTA of cta_mask.
+__device__ __forceinline__ void umma_commit_multicast(uint32_t bar, uint16_t cta_mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                     "r"(bar),
+                 "h"(cta_mask)
+                 : "memory");
 }
 
 // 16 columns of this warp's TMEM lane quarter, without waiting (see tmem_wait).
@@ -230,16 +272,17 @@ __device__ __forceinline__ void encode_point(const MlpArgs &A, long long p, int 
     const int Lf = A.pe_freqs;
     for (int g = g0 * 8; g < K0; g += gstep * 8) {  // 8 encoded values per 16-byte store
         float v[8];
+        // column 2 P + 0 / 1 holds sin / cos(2^j pi x_a) with P = a L + j
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int col = g + q;
-            float val = 0.0f;
-            if (valid && col < 6 * Lf) {
-                const int a = col / (2 * Lf), r = col % (2 * Lf), j = r >> 1;
-                const float arg = ldexpf(x[a], j);  // 2^j x, exact
-                val = (r & 1) ? cospif(arg) : sinpif(arg);
+        for (int q = 0; q < 4; ++q) {
+            const int P = (g >> 1) + q;
+            float sv = 0.0f, cv = 0.0f;
+            if (valid && P < 3 * Lf) {
+                const int a = P / Lf, j = P - a * Lf;
+                sincospif(ldexpf(x[a], j), &sv, &cv);  // 2^j x exact
             }
-            v[q] = val;
+            v[2 * q] = sv;
+            v[2 * q + 1] = cv;
         }
         uint4 pk;
         pk.x = pack_bf16(v[0], v[1]);
@@ -252,7 +295,7 @@ __device__ __forceinline__ void encode_point(const MlpArgs &A, long long p, int 
 
 __device__ __forceinline__ int n_chunks(int K) { return K / kChunkK; }  // K is padded to a multiple of 64
 
-__global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant__ MlpArgs A) {
+__global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
     extern __shared__ __align__(1024) char smem_raw[];
     // the swizzled operand tiles start on 1024-byte boundaries
     char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -276,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
     if (tid == 0) {
         for (int s = 0; s < kSlots; ++s) {
             mbar_init(full_bar(s), 1);
-            mbar_init(empty_bar(s), 1);
+            mbar_init(empty_bar(s), kCluster);  // one release per CTA of the cluster
         }
         for (int t = 0; t < kPair; ++t) {
             mbar_init(acc_full(t), 1);
@@ -294,13 +337,20 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    namespace cg = cooperative_groups;
+    const uint32_t crank = kCluster > 1 ? cg::this_cluster().block_rank() : 0u;
+    constexpr uint16_t kCtaMask = uint16_t((1u << kCluster) - 1u);
+    if (kCluster > 1) cg::this_cluster().sync();  // every CTA's barriers exist before any multicast
     const uint32_t tmem = *tmem_slot;
     // Tiles go to CTAs in groups of kPair: group r holds tiles (kPair r + t) * grid + bid, t < kPair;
     // a tile past the end is carried as an empty one (no outputs).
     const long long n_tiles = (A.n_points + kTileM - 1) / kTileM;
     const long long G = gridDim.x;
     auto pair_tile = [&](long long r, int t) { return (kPair * r + t) * G + blockIdx.x; };
-    const long long n_pairs = (n_tiles - blockIdx.x + kPair * G - 1) / (kPair * G);
+    // the same count for every CTA of a cluster (they share the weight stream); the cluster's first
+    // CTA has the most tiles, the others carry empty ones
+    const long long bid0 = (long long)blockIdx.x - crank;
+    const long long n_pairs = n_tiles > bid0 ? (n_tiles - bid0 + kPair * G - 1) / (kPair * G) : 0;
 
     if (warp == kProducerWarp) {
         if (lane == 0) {
@@ -318,11 +368,21 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
                                 break;
                             const uint32_t bytes = uint32_t(Ly.N) * uint32_t(kChunkK) * 2u;
                             mbar_expect_tx(full_bar(slot), bytes);
-                            bulk_g2s(smem_u32(ring) + uint32_t(slot) * kSlotBytes,
-                                     reinterpret_cast<const char *>(Ly.w) + size_t(c) * Ly.N * kChunkK * 2, bytes,
-                                     full_bar(slot));
+                            const char *src = reinterpret_cast<const char *>(Ly.w) + size_t(c) * Ly.N * kChunkK * 2;
+                            if (kCluster == 1) {
+                                bulk_g2s(smem_u32(ring) + uint32_t(slot) * kSlotBytes, src, bytes, full_bar(slot));
+                            } else {  // this CTA's slice, to every CTA of the cluster
+                                const uint32_t part = bytes / kCluster;
+                                bulk_g2s_multicast(smem_u32(ring) + uint32_t(slot) * kSlotBytes + crank * part,
+                                                   src + crank * part, part, full_bar(slot), kCtaMask);
+                            }
                         }
                     }
+            // Every CTA of the cluster has released the last use of each slot, so no
+            // release (a remote mbarrier arrive) is still travelling here at exit.
+            if (kCluster > 1)
+                for (long long j = it > kSlots ? it - kSlots : 0; j < it && !abort_flag; ++j)
+                    if (!mbar_wait(empty_bar(int(j % kSlots)), uint32_t((j / kSlots) & 1), A.err, &abort_flag)) break;
         }
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
@@ -349,7 +409,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
                                     smem_desc_sw128(smem_u32(ring) + uint32_t(slot) * kSlotBytes + uint32_t(s) * 32u);
                                 umma_bf16(d_tmem, ad, bd, idesc, (c > 0 || s > 0) ? 1u : 0u);
                             }
-                            umma_commit(empty_bar(slot));
+                            if (kCluster == 1) umma_commit(empty_bar(slot));
+                            else umma_commit_multicast(empty_bar(slot), kCtaMask);
                         }
                         if (abort_flag) break;
                         umma_commit(acc_full(t));
@@ -360,17 +421,19 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
         const int row = q * 32 + lane;
         long long uses = 0;
         bool stop = false;
+        long long pt[kPair];
+        // encode tile t of group r into A tile t (its previous tile's head has been read) and release it
+        auto encode_tile = [&](long long r, int t) {
+            const long long tile = pair_tile(r, t);
+            pt[t] = tile < n_tiles ? tile * kTileM + row : A.n_points;  // past the end: invalid row
+            encode_point(A, pt[t], row, sa + size_t(t) * kATileBytes, g, 4);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(a_ready(t));
+        };
+        if (n_pairs > 0)
+            for (int t = 0; t < kPair; ++t) encode_tile(0, t);
         for (long long r = 0; r < n_pairs && !stop; ++r) {
-            long long pt[kPair];
-#pragma unroll
-            for (int t = 0; t < kPair; ++t) {
-                const long long tile = pair_tile(r, t);
-                pt[t] = tile < n_tiles ? tile * kTileM + row : A.n_points;  // past the end: invalid row
-                encode_point(A, pt[t], row, sa + size_t(t) * kATileBytes, g, 4);
-                fence_proxy_async();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(a_ready(t));
-            }
             for (int li = 0; li < A.n_layers && !stop; ++li, ++uses) {
                 const MlpLayerDev &Ly = A.L[li];
                 const int N = Ly.N;
@@ -438,6 +501,18 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
                             }
                         }
                     };
+#if FNR_MLP_LD4
+                    for (int j0 = g; j0 < nj; j0 += 16) {  // warp-uniform: up to four loads per wait
+                        uint32_t rr[4][16];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (j0 + 4 * i < nj) tmem_ld16_nowait(trow + uint32_t((j0 + 4 * i) * 16), rr[i]);
+                        tmem_wait();
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (j0 + 4 * i < nj) process(rr[i], j0 + 4 * i);
+                    }
+#else
                     for (int j0 = g; j0 < nj; j0 += 8) {  // warp-uniform
                         uint32_t r0[16], r1[16];
                         const bool two = j0 + 4 < nj;
@@ -447,6 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
                         process(r0, j0);
                         if (two) process(r1, j0 + 4);
                     }
+#endif
                     if (!last) {  // K padding of the next layer: columns [N, roundup(N, 64)) are 0
                         const uint4 z = make_uint4(0u, 0u, 0u, 0u);
                         for (int c8 = N + 8 * g; c8 < ((N + 63) & ~63); c8 += 32)
@@ -459,12 +535,15 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_kernel(const __grid_constant_
                         if (lane == 0) mbar_arrive(a_ready(t));
                     } else {
                         __syncwarp();
+                        // the next group's tile t, encoded while the other tile is still in flight
+                        if (r + 1 < n_pairs) encode_tile(r + 1, t);
                     }
                 }
             }
         }
     }
     __syncthreads();
+    if (kCluster > 1) cg::this_cluster().sync();  // no CTA leaves while a peer may still address it
     if (warp == kMmaWarp) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
@@ -576,8 +655,33 @@ fnr_status run_mlp(const fnr_mlp *m, int mode, const fnr_cache_desc &d, const Ca
         cudaSuccess)
         return cuda_fail(e, "MLP smem attribute");
     const long long tiles = (A.n_points + kTileM - 1) / kTileM;
-    const int grid = int(tiles < num_sms ? tiles : num_sms);
-    mlp_kernel<<<grid, kThreads, kSmemBytes, s>>>(A);
+    if (kCluster == 1) {
+        const int grid = int(tiles < num_sms ? tiles : num_sms);
+        mlp_kernel<<<grid, kThreads, kSmemBytes, s>>>(A);
+    } else {
+        // one CTA per SM: as many whole clusters as fit at once, no more than the tiles need
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kCluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = kSmemBytes;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(unsigned(num_sms / kCluster * kCluster));
+        int max_clusters = 0;
+        if ((e = cudaOccupancyMaxActiveClusters(&max_clusters, mlp_kernel, &cfg)) != cudaSuccess)
+            return cuda_fail(e, "MLP cluster occupancy");
+        if (max_clusters < 1) return fail(FNR_ERR_UNSUPPORTED, "MLP kernel: no cluster of %d CTAs fits", kCluster);
+        long long clusters = (tiles + kCluster - 1) / kCluster;
+        if (clusters > max_clusters) clusters = max_clusters;
+        cfg.gridDim = dim3(unsigned(clusters * kCluster));
+        e = cudaLaunchKernelEx(&cfg, mlp_kernel, A);
+        if (e != cudaSuccess) return cuda_fail(e, "MLP launch");
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "MLP launch");
     int herr = 0;
     if ((e = cudaMemcpyAsync(&herr, ebuf.p, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
