@@ -136,6 +136,27 @@ def march_traffic(k: int):
     return MARCH_TRAFFIC["bytes_per_launch"]
 
 
+def unique_sector_bytes(w, sig, uvw, beta, cam):
+    """Bytes of the distinct 32-byte sectors one view touches (the "unique bytes" of a frame), counted
+    from the oracle's per-sample cells of every pixel: the density sectors of all in-box samples up to
+    termination, the record sectors of the occupied ones, the beta sectors of the rays' direction cells,
+    and the RGBA image. FP32 cache at D=8: 8 densities and exactly 3 records' worth of bytes per 3 sectors."""
+    import oracle
+    oc = oracle.Cache(w.k, w.D, w.l, sig, uvw, beta)
+    p = oracle.params_struct(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg)
+    _, st, cells = oracle.render_image(oc, cam, p, want_cells=True)
+    c = cells.reshape(-1)
+    c = c[c >= 0].astype(np.int64)
+    n_sig = np.unique(c >> 3).size                      # 8 binary32 densities per sector
+    occ = np.unique(c[sig.reshape(-1)[c] > 0])
+    rec = 3 * w.D * 4                                   # 96 bytes: 3 whole sectors per record
+    assert rec % 32 == 0
+    n_rec = occ.size * (rec // 32)
+    n_beta = np.unique(st[..., 3].reshape(-1)).size * ((w.D * 4 + 31) // 32)
+    return {"density_sectors": int(n_sig), "record_sectors": int(n_rec), "beta_sectors": int(n_beta),
+            "bytes": int(32 * (n_sig + n_rec + n_beta) + w.W * w.H * 16)}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -693,6 +714,11 @@ def run_fnr(args):
         }
     fnr.fnr_cache_free(ctx, cache)
     if rank == 0:
+        # distinct sectors the first view touches, from the oracle's cells (against the same launch time)
+        ub = unique_sector_bytes(w, sig, uvw, beta, cams[0])
+        out["roofline"]["unique_bytes_view0"] = ub["bytes"]
+        out["roofline"]["unique_frac"] = ub["bytes"] / (out["roofline"]["launch_ms"] * 1e-3) / 1e9 / \
+            out["roofline"]["peak"]
         if not args.no_extras:
             out["precision_forms"] = precision_forms(fnr, torch, ctx, w, sig, uvw, beta, cams, max(5, args.steps // 10))
             out["serving"] = serving_config(fnr, torch, dev, w, sig, uvw, beta, args.serve_seconds)

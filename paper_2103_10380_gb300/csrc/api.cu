@@ -289,6 +289,7 @@ void fill_frame(FrameDesc *f, const fnr_camera *cam, float *rgba, fnr_ray_stats 
     f->W = cam->width;
     f->H = cam->height;
     f->tiles_x = (cam->width + kTileW - 1) / kTileW;
+    if (FNR_TILE_2X2) f->tiles_x = (f->tiles_x + 1) / 2;  // groups of 2 x 2 tiles per row
     f->tile_begin = tile_begin;
     f->rgba = rgba;
     f->stats = stats;
@@ -296,7 +297,9 @@ void fill_frame(FrameDesc *f, const fnr_camera *cam, float *rgba, fnr_ray_stats 
 }
 
 int frame_tiles(const fnr_camera *cam) {
-    return ((cam->width + kTileW - 1) / kTileW) * ((cam->height + kTileH - 1) / kTileH);
+    const int tx = (cam->width + kTileW - 1) / kTileW, ty = (cam->height + kTileH - 1) / kTileH;
+    if (FNR_TILE_2X2) return 4 * ((tx + 1) / 2) * ((ty + 1) / 2);
+    return tx * ty;
 }
 
 bool cache_belongs(fnr_context *ctx, const fnr_cache *c) {

@@ -43,7 +43,7 @@ struct RenderConst {
     uint32_t flags;       // FNR_RENDER_* bits
 };
 
-// One view inside a launch. Tiles are 8 x 4 pixels, one warp each.
+// One view inside a launch. Tiles are kTileW x kTileH pixels (8 x 4), one warp each.
 struct FrameDesc {
     float c2w[12];
     float fx, fy, cx, cy;
@@ -55,8 +55,31 @@ struct FrameDesc {
     int32_t *cells;       // [H*W][N] or null
 };
 
-constexpr int kTileW = 8, kTileH = 4;
+#ifndef FNR_TILE_W
+#define FNR_TILE_W 8
+#endif
+constexpr int kTileW = FNR_TILE_W, kTileH = 32 / FNR_TILE_W;  // one warp per tile, one lane per pixel
+static_assert(kTileW * kTileH == 32 && (kTileW & (kTileW - 1)) == 0, "a tile is one warp");
+// FNR_TILE_2X2: tiles numbered in 2 x 2 groups (the four warps of a block
+// render a compact 2 x 2 patch of tiles) instead of row-major over the frame
+#ifndef FNR_TILE_2X2
+#define FNR_TILE_2X2 1
+#endif
 constexpr int kMaxFramesPerLaunch = 32;
+
+// Top-left pixel of frame tile t (tiles_x: tiles per row, or 2 x 2 groups per row).
+__host__ __device__ inline void tile_origin(const FrameDesc &F, int t, int &x0, int &y0) {
+#if FNR_TILE_2X2
+    const int g = t >> 2, w = t & 3;
+    const int gy = g / F.tiles_x, gx = g - gy * F.tiles_x;
+    x0 = (2 * gx + (w & 1)) * kTileW;
+    y0 = (2 * gy + (w >> 1)) * kTileH;
+#else
+    const int ty = t / F.tiles_x, tx = t - ty * F.tiles_x;
+    x0 = tx * kTileW;
+    y0 = ty * kTileH;
+#endif
+}
 
 struct MarchArgs {
     CacheView c;

@@ -33,9 +33,10 @@ __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC)) march_kernel
     while (f + 1 < A.n_frames && tile >= A.f[f + 1].tile_begin) ++f;
     const FrameDesc &F = A.f[f];
     const int t = tile - F.tile_begin;
-    const int ty = t / F.tiles_x, tx = t - ty * F.tiles_x;
+    int x0, y0;
+    tile_origin(F, t, x0, y0);
     const int lane = threadIdx.x & 31;
-    const int px = tx * kTileW + (lane & (kTileW - 1)), py = ty * kTileH + lane / kTileW;
+    const int px = x0 + (lane & (kTileW - 1)), py = y0 + lane / kTileW;
     __shared__ WarpQueue<D> queues[FNR_BLOCK / 32];
     march_tile_queued<PREC, D, SKIP>(A.c, A.r, F, px, py, px < F.W && py < F.H, queues[threadIdx.x >> 5]);
 }

@@ -62,8 +62,9 @@ __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
         while (f + 1 < A.n_frames && t >= A.f[f + 1].tile_begin) ++f;
         const FrameDesc &F = A.f[f];
         const int lt = t - F.tile_begin;
-        const int ty = lt / F.tiles_x, tx = lt - ty * F.tiles_x;
-        const int px = tx * kTileW + (lane & (kTileW - 1)), py = ty * kTileH + lane / kTileW;
+        int x0, y0;
+        tile_origin(F, lt, x0, y0);
+        const int px = x0 + (lane & (kTileW - 1)), py = y0 + lane / kTileW;
         dev::march_tile_queued<PREC, D, false>(A.c, A.r, F, px, py, px < F.W && py < F.H, queues[threadIdx.x >> 5]);
         __syncwarp();
         if (lane == 0) {

@@ -96,8 +96,9 @@ __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
         const int f = serve_frame_of(tab, nf, t);
         const ServeFrame &sf = tab.frames[f];
         const int lt = t - tab.tile_begin[f];
-        const int ty = lt / sf.f.tiles_x, tx = lt - ty * sf.f.tiles_x;
-        const int px = tx * kTileW + (lane & (kTileW - 1)), py = ty * kTileH + lane / kTileW;
+        int x0, y0;
+        tile_origin(sf.f, lt, x0, y0);
+        const int px = x0 + (lane & (kTileW - 1)), py = y0 + lane / kTileW;
         dev::march_tile_queued<PREC, D, SKIP>(sf.c, sf.r, sf.f, px, py, px < sf.f.W && py < sf.f.H, queues[warp]);
     }
     __syncthreads();  // the block's outputs are written

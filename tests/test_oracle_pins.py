@@ -463,3 +463,30 @@ def test_skip_empty_same_image_fewer_lookups(tiny_workload, tiny_arrays, brick):
     if brick == 1:  # single-cell bricks: only occupied samples are looked up
         assert np.array_equal(st2[..., 1], st2[..., 2])
     assert st2[..., 1].sum() < st[..., 1].sum()
+
+
+def test_unique_sector_count_brute_force(tiny_workload, tiny_arrays):
+    """bench.py's unique-bytes figure against sets of sector indices built sample by sample."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    w = tiny_workload
+    sig, uvw, beta = tiny_arrays
+    cam = w.cameras()[0]
+    got = bench.unique_sector_bytes(w, sig, uvw, beta, cam)
+    oc = oracle.Cache(w.k, w.D, w.l, sig, uvw, beta)
+    _, st, cells = oracle.render_image(oc, cam, oracle.params_struct(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg),
+                                       want_cells=True)
+    dens, recs, betas = set(), set(), set()
+    sflat = sig.reshape(-1)
+    for c in cells.reshape(-1).tolist():
+        if c < 0:
+            continue
+        dens.add((4 * c) // 32)
+        if sflat[c] > 0:
+            for b in range(96 * c, 96 * c + 96):
+                recs.add(b // 32)
+    for d in st[..., 3].reshape(-1).tolist():
+        for b in range(32 * d, 32 * d + 32):
+            betas.add(b // 32)
+    assert (got["density_sectors"], got["record_sectors"], got["beta_sectors"]) == (len(dens), len(recs), len(betas))
