@@ -233,6 +233,13 @@ typedef struct {
  * n_lookups counts only the density lookups made (in-box samples in occupied
  * bricks, up to termination). */
 #define FNR_RENDER_SKIP_EMPTY 1u
+/* Interpolated direction lookup (the paper samples F_view with interpolation,
+ * Section 4): beta bilinear in (theta, phi) between the bin centres
+ * theta_i = (i + 1/2) pi / l, phi_j = (j + 1/2) 2 pi / l, theta neighbours
+ * clamped at the poles, phi neighbours wrapping around 2 pi. The angles are
+ * binary32 atan2f values, so colours differ from an FP64 evaluation by up to
+ * ~1e-4 rather than 1e-5; dir_cell still reports the nearest bin. */
+#define FNR_RENDER_DIR_BILINEAR 2u
 
 typedef struct {
     int32_t n_steps;    /* samples visited (i + 1 of the terminating sample, else N) */

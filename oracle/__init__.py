@@ -42,7 +42,7 @@ class _Camera(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("t_near", ctypes.c_float), ("t_far", ctypes.c_float),
                 ("t_thr", ctypes.c_float), ("bg", ctypes.c_float * 3), ("act", ctypes.c_int32),
-                ("skip_empty", ctypes.c_int32)]
+                ("skip_empty", ctypes.c_int32), ("dir_bilinear", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -93,6 +93,8 @@ def lib():
         L.orc_mlp_forward.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_int64, P, P, ctypes.c_int]
         L.orc_mlp_forward.restype = ctypes.c_int
         L.orc_table_field.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P]
+        L.orc_beta_bilinear.argtypes = [P, P, P]
+        L.orc_beta_bilinear.restype = None
         L.orc_table_field.restype = None
         _lib = L
     return _lib
@@ -187,12 +189,13 @@ def camera_struct(cam: dict) -> _Camera:
 
 
 def params_struct(N, t_near=2.0, t_far=6.0, t_thr=1e-4, bg=(1.0, 1.0, 1.0), act=ACT_SIGMOID,
-                  skip_empty=False) -> _Params:
+                  skip_empty=False, dir_bilinear=False) -> _Params:
     p = _Params()
     p.N, p.t_near, p.t_far, p.t_thr = int(N), float(t_near), float(t_far), float(t_thr)
     p.bg[:] = [float(v) for v in bg]
     p.act = int(act)
     p.skip_empty = 1 if skip_empty else 0
+    p.dir_bilinear = 1 if dir_bilinear else 0
     return p
 
 
@@ -261,6 +264,14 @@ def ray(cam: dict, px: int, py: int):
     cs = camera_struct(cam)
     lib().orc_ray(ctypes.byref(cs), px, py, _p(d), _p(o))
     return d, o
+
+
+def beta_bilinear(cache: Cache, d) -> np.ndarray:
+    """The bilinearly interpolated direction weights (FP64) for the binary32 unit direction d."""
+    d = np.ascontiguousarray(d, dtype=np.float32)
+    out = np.zeros(cache.D)
+    lib().orc_beta_bilinear(ctypes.byref(cache._s), _p(d), _p(out))
+    return out
 
 
 def dir_cell(l: int, d) -> tuple:

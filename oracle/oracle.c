@@ -71,6 +71,7 @@ typedef struct {
     float bg[3];
     int32_t act;
     int32_t skip_empty; /* nonzero: samples in bricks without density are not looked up */
+    int32_t dir_bilinear; /* nonzero: beta interpolated bilinearly in (theta, phi) between bin centres */
 } orc_params;
 
 /* ------------------------------------------------------------ number formats */
@@ -327,6 +328,37 @@ void orc_table_field(int64_t cell, int want_uvw, double *sigma, double *uvw, voi
     }
 }
 
+static double stored_beta(const orc_cache *c, int64_t cell, int i) {
+    return c->dir_prec == ORC_FP16 ? orc_f16_decode(((const uint16_t *)c->beta)[cell * c->D + i])
+                                   : (double)((const float *)c->beta)[cell * c->D + i];
+}
+
+/* Interpolated direction lookup (Section 4 samples F_view with interpolation
+ * rather than nearest neighbour): beta bilinear in (theta, phi) between the
+ * bin centres theta_i = (i + 1/2) pi / l, phi_j = (j + 1/2) 2 pi / l, with
+ * theta from +z and phi = atan2(y, x) in [0, 2 pi). Continuous indices
+ * u = theta l / pi - 1/2, v = phi l / (2 pi) - 1/2; the theta neighbours are
+ * clamped to [0, l - 1] (no data beyond the poles), the phi neighbours wrap. */
+void orc_beta_bilinear(const orc_cache *c, const float d[3], double *beta) {
+    const double pi = 3.14159265358979323846264338327950288;
+    const int l = c->l;
+    const double x = d[0], y = d[1], z = d[2];
+    const double theta = atan2(sqrt(x * x + y * y), z);
+    double phi = atan2(y, x);
+    if (phi < 0.0) phi += 2.0 * pi;
+    const double u = theta * l / pi - 0.5, v = phi * l / (2.0 * pi) - 0.5;
+    const double fu = floor(u), fv = floor(v);
+    const double a = u - fu, b = v - fv;
+    int i0 = (int)fu, i1 = i0 + 1;
+    i0 = i0 < 0 ? 0 : (i0 > l - 1 ? l - 1 : i0);
+    i1 = i1 < 0 ? 0 : (i1 > l - 1 ? l - 1 : i1);
+    const int j0 = (((int)fv % l) + l) % l, j1 = (j0 + 1) % l;
+    for (int i = 0; i < c->D; ++i)
+        beta[i] = (1.0 - a) * (1.0 - b) * stored_beta(c, (int64_t)i0 * l + j0, i) +
+                  (1.0 - a) * b * stored_beta(c, (int64_t)i0 * l + j1, i) +
+                  a * (1.0 - b) * stored_beta(c, (int64_t)i1 * l + j0, i) + a * b * stored_beta(c, (int64_t)i1 * l + j1, i);
+}
+
 /* ------------------------------------------------------------ one ray */
 typedef struct {
     const orc_cache *c;
@@ -348,9 +380,11 @@ static void render_ray(const ray_ctx *X, int32_t px, int32_t py, double *rgba, i
     dir_cell_tab(c->l, X->ct, X->qp, d, &it, &ip);
     int64_t dcell = (int64_t)it * c->l + ip;
     double beta[16];
-    for (int i = 0; i < D; ++i)
-        beta[i] = c->dir_prec == ORC_FP16 ? orc_f16_decode(((const uint16_t *)c->beta)[dcell * D + i])
-                                          : (double)((const float *)c->beta)[dcell * D + i];
+    if (p->dir_bilinear) {
+        orc_beta_bilinear(c, d, beta);
+    } else {
+        for (int i = 0; i < D; ++i) beta[i] = stored_beta(c, dcell, i);
+    }
     double T = 1.0, C[3] = {0.0, 0.0, 0.0};
     int64_t S = 0;
     int32_t n_steps = N, n_look = 0, n_occ = 0;

@@ -251,7 +251,8 @@ fnr_status make_render_const(const fnr_render_params *p, RenderConst *rc) {
     if (isnan(p->t_thr)) return fail(FNR_ERR_INVALID_ARG, "t_thr is NaN");
     if (p->activation != FNR_ACT_SIGMOID && p->activation != FNR_ACT_IDENTITY)
         return fail(FNR_ERR_INVALID_ARG, "unknown activation %d", p->activation);
-    if ((p->flags & ~FNR_RENDER_SKIP_EMPTY) != 0u) return fail(FNR_ERR_INVALID_ARG, "unknown render flags 0x%x", p->flags);
+    if ((p->flags & ~(FNR_RENDER_SKIP_EMPTY | FNR_RENDER_DIR_BILINEAR)) != 0u)
+        return fail(FNR_ERR_INVALID_ARG, "unknown render flags 0x%x", p->flags);
     if (p->reserved != 0) return fail(FNR_ERR_INVALID_ARG, "reserved field must be 0");
     rc->N = p->n_samples;
     rc->t_near = p->t_near;

@@ -181,6 +181,39 @@ __device__ __forceinline__ int dir_cell(const CacheView &c, float dx, float dy, 
     return it * l + ip;
 }
 
+// Bilinear direction weights (FNR_RENDER_DIR_BILINEAR): beta interpolated in
+// (theta, phi) between the bin centres theta_i = (i + 1/2) pi / l and
+// phi_j = (j + 1/2) 2 pi / l, theta neighbours clamped at the poles, phi
+// neighbours wrapping around 2 pi. Kept out of line: once per ray, and its
+// libm calls would otherwise raise the march's register pressure.
+template <int D>
+__device__ __noinline__ void stage_beta_bilinear(const CacheView &c, float dx, float dy, float dz,
+                                                 float (*qbeta)[32], int lane) {
+    auto beta_at = [&](long long cell, int i) {
+        return c.dir_prec == FNR_PREC_FP16 ? __half2float(__ldg(static_cast<const __half *>(c.beta) + cell * D + i))
+                                           : __ldg(static_cast<const float *>(c.beta) + cell * D + i);
+    };
+    const float pi = 3.14159265358979f;
+    const float th = atan2f(sqrtf(dx * dx + dy * dy), dz);
+    float ph = atan2f(dy, dx);
+    if (ph < 0.0f) ph += 2.0f * pi;
+    const float u = th * (static_cast<float>(c.l) / pi) - 0.5f;
+    const float v = ph * (static_cast<float>(c.l) / (2.0f * pi)) - 0.5f;
+    const float fu = floorf(u), fv = floorf(v);
+    const float a = u - fu, b = v - fv;
+    const int i0 = min(max(static_cast<int>(fu), 0), c.l - 1);
+    const int i1 = min(max(static_cast<int>(fu) + 1, 0), c.l - 1);
+    int j0 = static_cast<int>(fv) % c.l;
+    if (j0 < 0) j0 += c.l;
+    const int j1 = j0 + 1 == c.l ? 0 : j0 + 1;
+    const long long c00 = (long long)i0 * c.l + j0, c01 = (long long)i0 * c.l + j1;
+    const long long c10 = (long long)i1 * c.l + j0, c11 = (long long)i1 * c.l + j1;
+    const float w00 = (1.0f - a) * (1.0f - b), w01 = (1.0f - a) * b, w10 = a * (1.0f - b), w11 = a * b;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+        qbeta[i][lane] = w00 * beta_at(c00, i) + w01 * beta_at(c01, i) + w10 * beta_at(c10, i) + w11 * beta_at(c11, i);
+}
+
 // Per-ray setup: a1 (ray), a2 (direction cell), and the per-ray affine
 // coefficients of the sample cells with the sample range that can reach the box.
 template <int PREC, int D>
@@ -191,8 +224,9 @@ struct RaySetup {
     int dcell;
     float sigma_scale;
 
+    // qbeta / lane: where this ray's D direction weights (unscaled) are staged
     __device__ __forceinline__ void init(const CacheView &c, const RenderConst &r, const FrameDesc &F, int px,
-                                         int py) {
+                                         int py, float (*qbeta)[32], int lane) {
         // a1: ray (binary32, fixed sequence)
         const float dcx = __fdiv_rn(__fsub_rn(__fadd_rn(static_cast<float>(px), 0.5f), F.cx), F.fx);
         const float dcy = -__fdiv_rn(__fsub_rn(__fadd_rn(static_cast<float>(py), 0.5f), F.cy), F.fy);
@@ -204,8 +238,9 @@ struct RaySetup {
         const float dd[3] = {__fdiv_rn(wx, len), __fdiv_rn(wy, len), __fdiv_rn(wz, len)};
         const float oo[3] = {F.c2w[3], F.c2w[7], F.c2w[11]};
 
-        // a2: direction cell (beta itself is read by the caller)
+        // a2: direction cell and beta
         dcell = dir_cell(c, dd[0], dd[1], dd[2]);
+        stage_beta(c, r, dd, qbeta, lane);
         sigma_scale = (PREC == FNR_PREC_FP8_E4M3) ? __ldg(c.scales) : 1.0f;
 
         // a3/a4 per ray: cell coordinates of sample i are g_a = fma(i + 1/2, e_a, f_a)
@@ -262,6 +297,24 @@ struct RaySetup {
         }
         in_lo = max(in_lo, i_lo);
         in_hi = min(in_hi, i_hi);
+    }
+
+    // The ray's D direction weights (unscaled; FP8 folds the channel scales at
+    // shading) into qbeta[i][lane]: the nearest bin's, or bilinear in
+    // (theta, phi) between bin centres (FNR_RENDER_DIR_BILINEAR).
+    __device__ __forceinline__ void stage_beta(const CacheView &c, const RenderConst &r, const float dd[3],
+                                               float (*qbeta)[32], int lane) const {
+        auto beta_at = [&](long long cell, int i) {
+            return c.dir_prec == FNR_PREC_FP16
+                       ? __half2float(__ldg(static_cast<const __half *>(c.beta) + cell * D + i))
+                       : __ldg(static_cast<const float *>(c.beta) + cell * D + i);
+        };
+        if (r.flags & FNR_RENDER_DIR_BILINEAR) {
+            stage_beta_bilinear<D>(c, dd[0], dd[1], dd[2], qbeta, lane);
+        } else {
+#pragma unroll
+            for (int i = 0; i < D; ++i) qbeta[i][lane] = beta_at(dcell, i);
+        }
     }
 
     // Cell of sample i (fi = i + 0.5) or -1 outside the box. For finite g,
@@ -371,22 +424,14 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
     const int lane = threadIdx.x & 31;
     RaySetup<PREC, D> R;
     if (active) {
-        R.init(c, r, F, px, py);
+        R.init(c, r, F, px, py, q.beta, lane);
     } else {
         R.i_lo = R.i_hi = 0;
         R.dcell = 0;
         R.sigma_scale = 1.0f;
     }
-    // unscaled beta of this lane's ray (FP8 folds the channel scales at shading)
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        float b = 0.0f;
-        if (active)
-            b = c.dir_prec == FNR_PREC_FP16
-                    ? __half2float(__ldg(static_cast<const __half *>(c.beta) + (long long)R.dcell * D + i))
-                    : __ldg(static_cast<const float *>(c.beta) + (long long)R.dcell * D + i);
-        q.beta[i][lane] = b;
-    }
+    if (!active)
+        for (int i = 0; i < D; ++i) q.beta[i][lane] = 0.0f;
     float T = 1.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
     long long S = 0;
     int n_look = 0, n_occ = 0, n_steps = r.N;

@@ -72,7 +72,7 @@ def gpu_render(fnr, ctx, cache, cams, params, with_cells=False, stream=None):
 
 def oparams(p):
     return oracle.params_struct(p.n_samples, p.t_near, p.t_far, p.t_thr, tuple(p.bg), p.activation,
-                                skip_empty=bool(p.flags & 1))
+                                skip_empty=bool(p.flags & 1), dir_bilinear=bool(p.flags & 2))
 
 
 def compare(got, ref, tol=TOL):

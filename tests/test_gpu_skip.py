@@ -61,7 +61,7 @@ def render(fnr, ctx, cache, cam, p, with_cells=True):
 
 def oparams(p):
     return oracle.params_struct(p.n_samples, p.t_near, p.t_far, p.t_thr, tuple(p.bg), p.activation,
-                                skip_empty=bool(p.flags & 1))
+                                skip_empty=bool(p.flags & 1), dir_bilinear=bool(p.flags & 2))
 
 
 def occupancy_from_device(lay, k):
@@ -135,7 +135,7 @@ def test_invalid_flags_and_bricks(fnr, ctx, tiny_workload, tiny_arrays):
         cam = w.cameras()[0]
         out = torch.zeros(cam["W"] * cam["H"] * 4, device="cuda")
         p = fnr.make_params(w.n_samples)
-        p.flags = 2
+        p.flags = 4  # no such flag
         with pytest.raises(fnr.FnrError) as ei:
             fnr.fnr_render(ctx, cache, [cam], p, out)
         assert ei.value.status == fnr.FNR_ERR_INVALID_ARG
@@ -161,7 +161,7 @@ def test_served_skip_requests(fnr, tiny_workload, tiny_arrays):
         cams = scenegen.cameras(77, 12, 53, 41)
         reqs = []
         for i, cam in enumerate(cams):
-            p = fnr.make_params(w.n_samples, skip_empty=(i % 2 == 0))
+            p = fnr.make_params(w.n_samples, skip_empty=(i % 2 == 0), dir_bilinear=(i % 3 == 0))
             n = cam["W"] * cam["H"]
             rgba = torch.zeros(n * 4, device="cuda")
             stats = torch.zeros(n * 4, device="cuda", dtype=torch.int32)

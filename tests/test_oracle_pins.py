@@ -490,3 +490,67 @@ def test_unique_sector_count_brute_force(tiny_workload, tiny_arrays):
         for b in range(32 * d, 32 * d + 32):
             betas.add(b // 32)
     assert (got["density_sectors"], got["record_sectors"], got["beta_sectors"]) == (len(dens), len(recs), len(betas))
+
+
+def _dir(theta, phi):
+    return np.array([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)], dtype=np.float32)
+
+
+def _angles(d):
+    x, y, z = (float(v) for v in d)
+    th = math.atan2(math.hypot(x, y), z)
+    ph = math.atan2(y, x)
+    return th, ph + 2 * math.pi if ph < 0 else ph
+
+
+def test_beta_bilinear_reproduces_linear_fields_and_centres():
+    """Bilinear interpolation in (theta, phi): exact at bin centres and for fields linear in the angles
+    between the first and last bin centres; a field of theta alone is clamped beyond the polar centres."""
+    l, D = 16, 3
+    th_c = (np.arange(l) + 0.5) * np.pi / l
+    ph_c = (np.arange(l) + 0.5) * 2 * np.pi / l
+    coef = np.array([[0.7, -0.2, 0.1], [0.3, 0.05, -1.0], [-0.4, 0.6, 0.25]])  # beta_i = a th + b ph + c
+    grid = (coef[None, None, :, 0] * th_c[:, None, None] + coef[None, None, :, 1] * ph_c[None, :, None] +
+            coef[None, None, :, 2]).astype(np.float64)
+    c = oracle.Cache(2, D, l, np.zeros(8, np.float32), np.zeros(8 * 3 * D, np.float32), grid.astype(np.float32))
+    g32 = grid.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(8)
+    for _ in range(200):
+        d = _dir(rng.uniform(th_c[0], th_c[-1]), rng.uniform(ph_c[0], ph_c[-1]))
+        th, ph = _angles(d)
+        want = coef[:, 0] * th + coef[:, 1] * ph + coef[:, 2]
+        # the grid holds binary32 values: compare with the interpolant of those
+        assert np.allclose(oracle.beta_bilinear(c, d), want, atol=2e-6)
+    for i, j in [(0, 0), (5, 9), (15, 15), (7, 0)]:
+        got = oracle.beta_bilinear(c, _dir(th_c[i], ph_c[j]))
+        assert np.allclose(got, g32[i, j], atol=1e-5)
+    # theta-only field: above the first centre (towards +z) the first row is used as is
+    rows = np.repeat(np.arange(l, dtype=np.float32)[:, None, None], l, axis=1).repeat(D, axis=2)
+    cr = oracle.Cache(2, D, l, np.zeros(8, np.float32), np.zeros(8 * 3 * D, np.float32), rows)
+    assert np.allclose(oracle.beta_bilinear(cr, _dir(0.3 * th_c[0], 1.0)), 0.0)
+    assert np.allclose(oracle.beta_bilinear(cr, _dir(np.pi - 0.3 * th_c[0], 4.0)), l - 1)
+
+
+def test_beta_bilinear_wraps_in_phi():
+    """Between the last and the first azimuth centre the weights wrap around 2 pi."""
+    l, D = 8, 1
+    grid = np.zeros((l, l, D), np.float32)
+    grid[:, 0, 0] = 1.0  # bin 0 in phi
+    c = oracle.Cache(2, D, l, np.zeros(8, np.float32), np.zeros(8 * 3, np.float32), grid)
+    th = np.pi / 2
+    w = 2 * np.pi / l
+    for frac in (0.1, 0.5, 0.9):  # phi between the centre of bin l-1 and 2 pi + centre of bin 0
+        ph = (l - 0.5) * w + frac * w
+        got = oracle.beta_bilinear(c, _dir(th, ph % (2 * np.pi)))[0]
+        assert abs(got - frac) < 1e-5, (frac, got)
+
+
+def test_bilinear_render_with_constant_beta_equals_nearest(tiny_workload, tiny_arrays):
+    w = tiny_workload
+    sig, uvw, _ = tiny_arrays
+    beta = np.broadcast_to(np.linspace(-1, 1, w.D, dtype=np.float32), (w.l, w.l, w.D)).copy()
+    c = oracle.Cache(w.k, w.D, w.l, sig, uvw, beta)
+    cam = w.cameras()[0]
+    a = oracle.render_image(c, cam, oracle.params_struct(w.n_samples))
+    b = oracle.render_image(c, cam, oracle.params_struct(w.n_samples, dir_bilinear=True))
+    assert np.array_equal(a[1], b[1]) and np.allclose(a[0], b[0], atol=1e-12)
