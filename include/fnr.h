@@ -83,6 +83,7 @@ typedef int32_t fnr_status;
 #define FNR_ERR_TIMEOUT 7     /* a host wait ran out */
 #define FNR_ERR_CUDA 8        /* a CUDA runtime call failed */
 #define FNR_ERR_DEVICE 9      /* a kernel reported an error through its status word */
+#define FNR_ERR_IO 10         /* a file could not be read or written, or is not a cache file */
 
 #define FNR_PREC_FP32 0
 #define FNR_PREC_FP16 1
@@ -206,6 +207,20 @@ typedef struct {
     uint64_t footprint;        /* device bytes */
 } fnr_cache_layout;
 FNR_API fnr_status fnr_cache_get_layout(const fnr_cache *cache, fnr_cache_layout *out);
+
+/* Persist a built cache (no counterpart in the paper, which keeps its caches
+ * in memory): the file holds a header -- the 8 bytes "FNRCACHE", a uint32
+ * format version (1), the uint32 header size, the fnr_cache_desc and the
+ * uint64 device footprint -- followed by the cache's device allocation byte
+ * for byte (every section of fnr_cache_layout, whose offsets follow from the
+ * descriptor). Saving reads the device through a pinned staging buffer after
+ * synchronising the context's device. Errors: INVALID_ARG, IO, CUDA. */
+FNR_API fnr_status fnr_cache_save(const fnr_cache *cache, const char *path);
+/* Load a saved cache into ctx (charged against its budget like a build) and
+ * upload it on `stream`; the call returns after the upload. Errors:
+ * INVALID_ARG, IO (unreadable, truncated, wrong magic / version / size),
+ * BUDGET, CUDA. */
+FNR_API fnr_status fnr_cache_load(fnr_context *ctx, const char *path, fnr_stream_t stream, fnr_cache **out);
 
 /* ------------------------------------------------------------------ rendering */
 typedef struct {

@@ -24,6 +24,7 @@ FNR_ERR_NOT_READY = 6
 FNR_ERR_TIMEOUT = 7
 FNR_ERR_CUDA = 8
 FNR_ERR_DEVICE = 9
+FNR_ERR_IO = 10
 
 FNR_PREC_FP32 = 0
 FNR_PREC_FP16 = 1
@@ -38,7 +39,7 @@ FNR_LOC_HOST = 0
 FNR_LOC_DEVICE = 1
 
 _STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "BUDGET", 5: "QUEUE_FULL",
-                 6: "NOT_READY", 7: "TIMEOUT", 8: "CUDA", 9: "DEVICE"}
+                 6: "NOT_READY", 7: "TIMEOUT", 8: "CUDA", 9: "DEVICE", 10: "IO"}
 
 
 class FnrError(RuntimeError):
@@ -118,6 +119,8 @@ SIGNATURES = {
                          ctypes.POINTER(_P)], ctypes.c_int32),
     "fnr_cache_free": ([_P, _P], ctypes.c_int32),
     "fnr_cache_get_layout": ([_P, ctypes.POINTER(fnr_cache_layout)], ctypes.c_int32),
+    "fnr_cache_save": ([_P, ctypes.c_char_p], ctypes.c_int32),
+    "fnr_cache_load": ([_P, ctypes.c_char_p, _P, ctypes.POINTER(_P)], ctypes.c_int32),
     "fnr_render": ([_P, _P, ctypes.POINTER(fnr_camera), ctypes.c_int32, ctypes.POINTER(fnr_render_params), _P, _P,
                     _P, _P], ctypes.c_int32),
     "fnr_serve_start": ([_P, ctypes.POINTER(fnr_serve_config)], ctypes.c_int32),
@@ -254,6 +257,16 @@ def fnr_cache_get_layout(cache: int) -> fnr_cache_layout:
     out = fnr_cache_layout()
     check(lib().fnr_cache_get_layout(cache, ctypes.byref(out)))
     return out
+
+
+def fnr_cache_save(cache: int, path) -> None:
+    check(lib().fnr_cache_save(cache, os.fsencode(path)))
+
+
+def fnr_cache_load(ctx: int, path, stream=None) -> int:
+    out = _P()
+    check(lib().fnr_cache_load(ctx, os.fsencode(path), _stream_handle(stream), ctypes.byref(out)))
+    return out.value
 
 
 def make_camera(cam: dict) -> fnr_camera:

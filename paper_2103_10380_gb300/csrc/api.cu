@@ -472,6 +472,124 @@ fnr_status fnr_cache_free(fnr_context *ctx, fnr_cache *c) {
     return FNR_OK;
 }
 
+// ---------------------------------------------------------------- save / load
+namespace {
+constexpr char kFileMagic[8] = {'F', 'N', 'R', 'C', 'A', 'C', 'H', 'E'};
+constexpr uint32_t kFileVersion = 1;
+struct FileHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    fnr_cache_desc desc;
+    uint64_t footprint;
+};
+constexpr size_t kStageBytes = size_t(64) << 20;  // pinned staging buffer
+
+struct PinnedBuf {
+    void *p = nullptr;
+    ~PinnedBuf() {
+        if (p) cudaFreeHost(p);
+    }
+};
+struct File {
+    FILE *f = nullptr;
+    ~File() {
+        if (f) fclose(f);
+    }
+};
+}  // namespace
+
+fnr_status fnr_cache_save(const fnr_cache *c, const char *path) {
+    clear_error();
+    if (!c || !path) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e = cudaSetDevice(c->ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "synchronise before save");
+    FileHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kFileMagic, 8);
+    h.version = kFileVersion;
+    h.header_bytes = sizeof(FileHeader);
+    h.desc = c->desc;
+    h.footprint = c->footprint;
+    File F;
+    if (!(F.f = fopen(path, "wb"))) return fail(FNR_ERR_IO, "cannot open %s for writing", path);
+    if (fwrite(&h, sizeof(h), 1, F.f) != 1) return fail(FNR_ERR_IO, "write failed: %s", path);
+    PinnedBuf buf;
+    if ((e = cudaMallocHost(&buf.p, kStageBytes)) != cudaSuccess) return cuda_fail(e, "staging buffer");
+    const char *src = static_cast<const char *>(c->base);
+    for (uint64_t off = 0; off < c->footprint; off += kStageBytes) {
+        const size_t n = size_t(std::min<uint64_t>(kStageBytes, c->footprint - off));
+        if ((e = cudaMemcpy(buf.p, src + off, n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "cache read-back");
+        if (fwrite(buf.p, 1, n, F.f) != n) return fail(FNR_ERR_IO, "write failed: %s", path);
+    }
+    if (fflush(F.f) != 0) return fail(FNR_ERR_IO, "write failed: %s", path);
+    return FNR_OK;
+}
+
+fnr_status fnr_cache_load(fnr_context *ctx, const char *path, fnr_stream_t stream, fnr_cache **out) {
+    clear_error();
+    if (!ctx || !path || !out) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    File F;
+    if (!(F.f = fopen(path, "rb"))) return fail(FNR_ERR_IO, "cannot open %s", path);
+    FileHeader h;
+    if (fread(&h, sizeof(h), 1, F.f) != 1) return fail(FNR_ERR_IO, "%s: truncated header", path);
+    if (memcmp(h.magic, kFileMagic, 8) != 0) return fail(FNR_ERR_IO, "%s is not a cache file", path);
+    if (h.version != kFileVersion || h.header_bytes != sizeof(FileHeader))
+        return fail(FNR_ERR_IO, "%s: format version %u is not supported", path, h.version);
+    if (!desc_valid(&h.desc)) return fail(FNR_ERR_IO, "%s: invalid cache descriptor", path);
+    const Layout L = layout_of(&h.desc);
+    if (h.footprint != L.total)
+        return fail(FNR_ERR_IO, "%s: footprint %llu does not match the descriptor's %llu", path,
+                    (unsigned long long)h.footprint, (unsigned long long)L.total);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if (!budget_charge(ctx, L.total))
+        return fail(FNR_ERR_BUDGET, "cache needs %llu bytes, budget %llu, in use %llu", (unsigned long long)L.total,
+                    (unsigned long long)ctx->budget, (unsigned long long)ctx->used.load());
+    fnr_cache *c = new fnr_cache();
+    c->desc = h.desc;
+    c->footprint = L.total;
+    c->ctx = ctx;
+    fnr_status st = FNR_OK;
+    if ((e = cudaMalloc(&c->base, L.total)) != cudaSuccess) {
+        budget_uncharge(ctx, L.total);
+        delete c;
+        return cuda_fail(e, "cache allocation");
+    }
+    {
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        PinnedBuf buf;
+        if ((e = cudaMallocHost(&buf.p, kStageBytes)) != cudaSuccess) st = cuda_fail(e, "staging buffer");
+        char *dst = static_cast<char *>(c->base);
+        for (uint64_t off = 0; st == FNR_OK && off < L.total; off += kStageBytes) {
+            const size_t n = size_t(std::min<uint64_t>(kStageBytes, L.total - off));
+            if (fread(buf.p, 1, n, F.f) != n) {
+                st = fail(FNR_ERR_IO, "%s: truncated payload", path);
+                break;
+            }
+            if ((e = cudaMemcpyAsync(dst + off, buf.p, n, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(s)) != cudaSuccess)  // the staging buffer is reused
+                st = cuda_fail(e, "cache upload");
+        }
+    }
+    if (st != FNR_OK) {
+        cudaFree(c->base);
+        budget_uncharge(ctx, L.total);
+        delete c;
+        return st;
+    }
+    fill_view(c, L);
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->caches.insert(c);
+    }
+    *out = c;
+    return FNR_OK;
+}
+
 fnr_status fnr_cache_get_layout(const fnr_cache *c, fnr_cache_layout *out) {
     clear_error();
     if (!c || !out) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
