@@ -658,7 +658,31 @@ def run_fnr(args):
     k1.record(stream)
     torch.cuda.synchronize()
     sk_launch_ms = k0.elapsed_time(k1) / (sk_steps * w.n_cams)
-    del rgba_skip, stats_skip
+
+    # the same scene as a sparse brick cache (FNR_LAYOUT_BRICKS, always skipping)
+    bdesc = fnr.make_desc(w.k, w.D, w.l, fnr.FNR_PREC_FP32, fnr.FNR_PREC_FP32, layout=fnr.FNR_LAYOUT_BRICKS)
+    bcache = fnr.fnr_build_cache(ctx, bdesc, sig.reshape(-1), uvw.reshape(-1), beta.reshape(-1))
+    blay = fnr.fnr_cache_get_layout(bcache)
+    rgba_b = torch.empty_like(rgba)
+    fnr.fnr_render(ctx, bcache, fcams[:1], params_skip, rgba_b[0], None, stream=stream)
+    torch.cuda.synchronize()
+    bricks_identical = bool(torch.equal(rgba_b[0], rgba_skip[0]))
+    for _ in range(3):
+        for i in range(w.n_cams):
+            fnr.fnr_render(ctx, bcache, [fcams[i]], params_skip, rgba_b[i], None, stream=stream)
+    k0.record(stream)
+    for s_ in range(sk_steps):
+        for i in range(w.n_cams):
+            fnr.fnr_render(ctx, bcache, [fcams[i]], params_skip, rgba_b[i], None, stream=stream)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    br_launch_ms = k0.elapsed_time(k1) / (sk_steps * w.n_cams)
+    bricks_line = {"mrays_per_s": npix / (br_launch_ms * 1e-3) / 1e6, "launch_ms": br_launch_ms,
+                   "cache_bytes": int(blay.footprint), "dense_cache_bytes": int(fnr.fnr_cache_footprint(desc)),
+                   "bricks": int(blay.n_bricks), "brick": int(blay.occupancy_brick),
+                   "image_bit_identical_to_dense_skip": bricks_identical}
+    fnr.fnr_cache_free(ctx, bcache)
+    del rgba_skip, stats_skip, rgba_b
 
     # the same 8 views in one launch (fnr_render takes several cameras): no per-launch tail
     for _ in range(3):
@@ -704,6 +728,7 @@ def run_fnr(args):
                              "frac": alg_skip / (sk_launch_ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"]),
                              "algorithmic_bytes_per_launch": alg_skip,
                              "bytes": "densities looked up + records of occupied samples + beta + RGBA + brick bits"}},
+            "bricks_layout": bricks_line,
             "all_views_one_launch": {
                 "mrays_per_s": w.n_cams * npix / (mv_ms * 1e-3) / 1e6, "launch_ms": mv_ms,
                 "roofline_frac": alg_per_launch * w.n_cams / (mv_ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"])},

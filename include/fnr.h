@@ -132,8 +132,20 @@ typedef struct {
     int32_t occupancy_brick; /* cells per side of an occupancy brick (FNR_RENDER_SKIP_EMPTY):
                                 a power of two 1..256, or 0 = the smallest power of two >= 2
                                 with ceil(k / B) <= 64 (8 at k = 512, 16 at k = 1024) */
+    int32_t layout;        /* FNR_LAYOUT_DENSE or FNR_LAYOUT_BRICKS */
+    int32_t reserved;      /* must be 0 */
     float bmin[3], bmax[3]; /* bounding box V, bmax > bmin on every axis */
 } fnr_cache_desc;
+
+/* Storage of the position cache. DENSE: the k^3 sigma plane and k^3 records.
+ * BRICKS (sparse; the paper stores its caches sparsely, Section 3.3 and the
+ * supplementary cache sizes): only the occupancy bricks (B^3 cells, B =
+ * occupancy_brick) holding a stored density > 0 keep their sigma and records,
+ * in a pool of bricks reached through a page table of ceil(k / B)^3 entries.
+ * Renders from a BRICKS cache have FNR_RENDER_SKIP_EMPTY semantics whether or
+ * not the flag is set (an empty brick has no storage). */
+#define FNR_LAYOUT_DENSE 0
+#define FNR_LAYOUT_BRICKS 1
 
 /* One MLP for the tensor-core cache build (Section 3.2, Eqs. 3 and 4; Section 4):
  * input = positional encoding gamma(x) = [sin(2^j pi x_a), cos(2^j pi x_a)],
@@ -177,8 +189,12 @@ typedef struct {
  * s_uvw is one (u_i, v_i, w_i) triple; FP8 adds its (1 + 3D) binary32 scales.
  * Returns 0 for an invalid descriptor. */
 FNR_API uint64_t fnr_cache_bytes(const fnr_cache_desc *desc);
-/* Device bytes one cache occupies: the above plus record padding to 16 bytes
- * (8 for FP8), 256-byte section alignment and the two direction-bin tables. */
+/* Device bytes one dense cache occupies: the above plus record padding to 16
+ * bytes (8 for FP8), 256-byte section alignment, the two direction-bin tables
+ * and the occupancy bits. For FNR_LAYOUT_BRICKS it is the bound with every
+ * brick stored; a built cache reports its own footprint (fnr_cache_get_layout).
+ * A BRICKS build passes through a dense cache, which is charged to the budget
+ * while it exists. */
 FNR_API uint64_t fnr_cache_footprint(const fnr_cache_desc *desc);
 
 /* Build a cache on `stream`. Returns when the cache is complete (the call
@@ -205,13 +221,21 @@ typedef struct {
     int32_t record_stride;     /* bytes between (u, v, w) records */
     int32_t occupancy_brick;   /* B */
     uint64_t footprint;        /* device bytes */
+    int32_t layout;            /* FNR_LAYOUT_*; for BRICKS, sigma_dev and uvw_dev hold n_bricks
+                                  bricks of B^3 cells each, cell (x, y, z) of brick slot s at index
+                                  s B^3 + ((z mod B) B + (y mod B)) B + (x mod B) */
+    int32_t reserved1;
+    const int32_t *page_table_dev; /* BRICKS: [nb^3] brick slot, -1 for an empty brick (same brick
+                                      index as the occupancy bits); NULL for DENSE */
+    uint64_t n_bricks;         /* BRICKS: bricks stored */
 } fnr_cache_layout;
 FNR_API fnr_status fnr_cache_get_layout(const fnr_cache *cache, fnr_cache_layout *out);
 
 /* Persist a built cache (no counterpart in the paper, which keeps its caches
  * in memory): the file holds a header -- the 8 bytes "FNRCACHE", a uint32
- * format version (1), the uint32 header size, the fnr_cache_desc and the
- * uint64 device footprint -- followed by the cache's device allocation byte
+ * format version (1), the uint32 header size, the fnr_cache_desc, the uint64
+ * device footprint and the uint64 brick count (FNR_LAYOUT_BRICKS; else 0) --
+ * followed by the cache's device allocation byte
  * for byte (every section of fnr_cache_layout, whose offsets follow from the
  * descriptor). Saving reads the device through a pinned staging buffer after
  * synchronising the context's device. Errors: INVALID_ARG, IO, CUDA. */

@@ -33,6 +33,8 @@ FNR_ACT_SIGMOID = 0
 FNR_ACT_IDENTITY = 1
 FNR_RENDER_SKIP_EMPTY = 1
 FNR_RENDER_DIR_BILINEAR = 2
+FNR_LAYOUT_DENSE = 0
+FNR_LAYOUT_BRICKS = 1
 FNR_SRC_ARRAYS = 1
 FNR_SRC_MLP = 2
 FNR_LOC_HOST = 0
@@ -51,7 +53,8 @@ class FnrError(RuntimeError):
 class fnr_cache_desc(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("D", ctypes.c_int32), ("l", ctypes.c_int32),
                 ("pos_precision", ctypes.c_int32), ("dir_precision", ctypes.c_int32),
-                ("occupancy_brick", ctypes.c_int32), ("bmin", ctypes.c_float * 3), ("bmax", ctypes.c_float * 3)]
+                ("occupancy_brick", ctypes.c_int32), ("layout", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("bmin", ctypes.c_float * 3), ("bmax", ctypes.c_float * 3)]
 
 
 class fnr_mlp(ctypes.Structure):
@@ -69,7 +72,9 @@ class fnr_cache_layout(ctypes.Structure):
     _fields_ = [("sigma_dev", ctypes.c_void_p), ("uvw_dev", ctypes.c_void_p), ("beta_dev", ctypes.c_void_p),
                 ("scales_dev", ctypes.c_void_p), ("cos_theta_dev", ctypes.c_void_p),
                 ("phi_key_dev", ctypes.c_void_p), ("occupancy_dev", ctypes.c_void_p),
-                ("record_stride", ctypes.c_int32), ("occupancy_brick", ctypes.c_int32), ("footprint", ctypes.c_uint64)]
+                ("record_stride", ctypes.c_int32), ("occupancy_brick", ctypes.c_int32), ("footprint", ctypes.c_uint64),
+                ("layout", ctypes.c_int32), ("reserved1", ctypes.c_int32), ("page_table_dev", ctypes.c_void_p),
+                ("n_bricks", ctypes.c_uint64)]
 
 
 class fnr_camera(ctypes.Structure):
@@ -178,11 +183,12 @@ def fnr_context_used_bytes(ctx: int) -> int:
 
 
 def make_desc(k, D, l, pos_precision=FNR_PREC_FP32, dir_precision=FNR_PREC_FP32, bmin=(-1.5, -1.5, -1.5),
-              bmax=(1.5, 1.5, 1.5), occupancy_brick=0) -> fnr_cache_desc:
+              bmax=(1.5, 1.5, 1.5), occupancy_brick=0, layout=FNR_LAYOUT_DENSE) -> fnr_cache_desc:
     d = fnr_cache_desc()
     d.k, d.D, d.l = k, D, l
     d.pos_precision, d.dir_precision = pos_precision, dir_precision
     d.occupancy_brick = int(occupancy_brick)
+    d.layout = int(layout)
     d.bmin[:] = [float(v) for v in bmin]
     d.bmax[:] = [float(v) for v in bmax]
     return d

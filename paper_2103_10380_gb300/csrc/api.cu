@@ -41,7 +41,7 @@ int rec_stride_bytes(int prec, int D) {
 static uint64_t align256(uint64_t v) { return (v + 255u) & ~uint64_t(255u); }
 
 struct Layout {
-    uint64_t off_sigma, off_uvw, off_beta, off_ct, off_qp, off_scales, off_occ, total;
+    uint64_t off_sigma, off_uvw, off_beta, off_ct, off_qp, off_scales, off_occ, off_page, total;
     int rec_stride;
 };
 
@@ -72,12 +72,19 @@ static bool desc_valid(const fnr_cache_desc *d) {
         if (!(isfinite(d->bmin[a]) && isfinite(d->bmax[a]) && d->bmax[a] > d->bmin[a])) return false;
     const int B = d->occupancy_brick;
     if (B < 0 || B > 256 || (B & (B - 1)) != 0) return false;
+    if ((d->layout != FNR_LAYOUT_DENSE && d->layout != FNR_LAYOUT_BRICKS) || d->reserved != 0) return false;
     return true;
 }
 
-static Layout layout_of(const fnr_cache_desc *d) {
+// Sections of one cache allocation. Dense: k^3 densities and records. Bricks
+// (n_bricks >= 0): pools of n_bricks * B^3 densities and records, then the
+// page table after the occupancy bits.
+static Layout layout_of(const fnr_cache_desc *d, int64_t n_bricks = -1) {
     Layout L;
-    const uint64_t k3 = uint64_t(d->k) * d->k * d->k;
+    const bool bricks = d->layout == FNR_LAYOUT_BRICKS && n_bricks >= 0;
+    const int sh = occupancy_shift(d);
+    const uint64_t nb = uint64_t((d->k + (1 << sh) - 1) >> sh);
+    const uint64_t k3 = bricks ? uint64_t(n_bricks) << (3 * sh) : uint64_t(d->k) * d->k * d->k;
     L.rec_stride = rec_stride_bytes(d->pos_precision, d->D);
     uint64_t off = 0;
     L.off_sigma = off;
@@ -94,6 +101,8 @@ static Layout layout_of(const fnr_cache_desc *d) {
     off = align256(off + uint64_t(1 + 3 * d->D) * 4);
     L.off_occ = off;
     off = align256(off + occupancy_words(d) * 4);
+    L.off_page = off;
+    if (bricks) off = align256(off + nb * nb * nb * 4);
     L.total = off;
     return L;
 }
@@ -225,6 +234,8 @@ static void fill_view(fnr_cache *c, const Layout &L) {
     v.qp = reinterpret_cast<const float *>(base + L.off_qp);
     v.scales = reinterpret_cast<const float *>(base + L.off_scales);
     v.occ = reinterpret_cast<const uint32_t *>(base + L.off_occ);
+    v.layout = c->n_bricks > 0 || d.layout == FNR_LAYOUT_BRICKS ? FNR_LAYOUT_BRICKS : FNR_LAYOUT_DENSE;
+    v.page = v.layout == FNR_LAYOUT_BRICKS ? reinterpret_cast<const int32_t *>(base + L.off_page) : nullptr;
     v.occ_shift = occupancy_shift(&d);
     v.occ_dim = (d.k + (1 << v.occ_shift) - 1) >> v.occ_shift;
     for (int a = 0; a < 3; ++a) {
@@ -373,12 +384,94 @@ uint64_t fnr_cache_footprint(const fnr_cache_desc *d) {
     return layout_of(d).total;
 }
 
+// Dense cache -> FNR_LAYOUT_BRICKS cache: pool slots in brick-index order of
+// the occupied bricks, densities and records gathered brick by brick on the
+// GPU; the direction cache, tables, scales and occupancy bits are copied.
+static fnr_status make_bricks(fnr_context *ctx, const fnr_cache *dense, const fnr_cache_desc *desc,
+                              cudaStream_t s, fnr_cache **out) {
+    const CacheView &dv = dense->view;
+    const int64_t nb = dv.occ_dim, nb3 = nb * nb * nb;
+    std::vector<uint32_t> words(occupancy_words(desc));
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(words.data(), dv.occ, words.size() * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "occupancy read-back");
+    std::vector<int32_t> page(size_t(nb3), -1), slot_brick;
+    for (int64_t b = 0; b < nb3; ++b)
+        if ((words[size_t(b >> 5)] >> (b & 31)) & 1u) {
+            page[size_t(b)] = int32_t(slot_brick.size());
+            slot_brick.push_back(int32_t(b));
+        }
+    const int64_t n_bricks = int64_t(slot_brick.size());
+    const Layout L = layout_of(desc, n_bricks);
+    const Layout LD = layout_of(&dense->desc);
+    if (!budget_charge(ctx, L.total))
+        return fail(FNR_ERR_BUDGET, "brick cache needs %llu bytes, budget %llu, in use %llu",
+                    (unsigned long long)L.total, (unsigned long long)ctx->budget,
+                    (unsigned long long)ctx->used.load());
+    fnr_cache *c = new fnr_cache();
+    c->desc = *desc;
+    c->footprint = L.total;
+    c->n_bricks = uint64_t(n_bricks);
+    c->ctx = ctx;
+    if ((e = cudaMalloc(&c->base, L.total)) != cudaSuccess) {
+        budget_uncharge(ctx, L.total);
+        delete c;
+        return cuda_fail(e, "brick cache allocation");
+    }
+    char *base = static_cast<char *>(c->base);
+    const char *dbase = static_cast<const char *>(dense->base);
+    DevBuf slots;
+    fnr_status st = FNR_OK;
+    if (n_bricks > 0 && (e = cudaMalloc(&slots.p, size_t(n_bricks) * 4)) != cudaSuccess) st = cuda_fail(e, "slots");
+    if (st == FNR_OK &&
+        ((n_bricks > 0 && (e = cudaMemcpyAsync(slots.p, slot_brick.data(), size_t(n_bricks) * 4,
+                                               cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
+         (e = cudaMemcpyAsync(base + L.off_page, page.data(), size_t(nb3) * 4, cudaMemcpyHostToDevice, s)) !=
+             cudaSuccess ||
+         (e = cudaMemcpyAsync(base + L.off_beta, dbase + LD.off_beta, L.off_page - L.off_beta,
+                              cudaMemcpyDeviceToDevice, s)) != cudaSuccess))
+        st = cuda_fail(e, "brick cache tables");
+    // (beta, the bin tables, the scales and the occupancy bits keep their relative offsets)
+    if (st == FNR_OK && n_bricks > 0 &&
+        (e = launch_gather_bricks(dv.sigma, dv.uvw, base + L.off_sigma, base + L.off_uvw,
+                                  static_cast<const int32_t *>(slots.p), n_bricks, desc->k, dv.occ_shift,
+                                  dv.occ_dim, int(elem_bytes(desc->pos_precision)), L.rec_stride, s)) != cudaSuccess)
+        st = cuda_fail(e, "brick gather");
+    if (st == FNR_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "brick cache sync");
+    if (st != FNR_OK) {
+        cudaFree(c->base);
+        budget_uncharge(ctx, L.total);
+        delete c;
+        return st;
+    }
+    fill_view(c, L);
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->caches.insert(c);
+    }
+    *out = c;
+    return FNR_OK;
+}
+
 fnr_status fnr_build_cache(fnr_context *ctx, const fnr_cache_desc *desc, const fnr_cache_source *src,
                            fnr_stream_t stream, fnr_cache **out) {
     clear_error();
     if (!ctx || !desc || !src || !out) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     if (!desc_valid(desc)) return fail(FNR_ERR_INVALID_ARG, "invalid cache descriptor");
+    if (desc->layout == FNR_LAYOUT_BRICKS) {  // through a dense cache, freed afterwards
+        fnr_cache_desc dd = *desc;
+        dd.layout = FNR_LAYOUT_DENSE;
+        fnr_cache *dense = nullptr;
+        fnr_status st = fnr_build_cache(ctx, &dd, src, stream, &dense);
+        if (st != FNR_OK) return st;
+        st = make_bricks(ctx, dense, desc, reinterpret_cast<cudaStream_t>(stream), out);
+        std::string msg = st != FNR_OK ? std::string(fnr_last_error()) : std::string();
+        fnr_cache_free(ctx, dense);
+        if (st != FNR_OK) return fail(st, "%s", msg.c_str());
+        return FNR_OK;
+    }
     fnr_status st0;
     if (src->kind == FNR_SRC_MLP) {
         if ((st0 = check_mlp(src->pos_mlp, 1 + 3 * desc->D, "pos_mlp")) != FNR_OK) return st0;
@@ -482,6 +575,7 @@ struct FileHeader {
     uint32_t header_bytes;
     fnr_cache_desc desc;
     uint64_t footprint;
+    uint64_t n_bricks;  // FNR_LAYOUT_BRICKS: bricks in the pools
 };
 constexpr size_t kStageBytes = size_t(64) << 20;  // pinned staging buffer
 
@@ -512,6 +606,7 @@ fnr_status fnr_cache_save(const fnr_cache *c, const char *path) {
     h.header_bytes = sizeof(FileHeader);
     h.desc = c->desc;
     h.footprint = c->footprint;
+    h.n_bricks = c->n_bricks;
     File F;
     if (!(F.f = fopen(path, "wb"))) return fail(FNR_ERR_IO, "cannot open %s for writing", path);
     if (fwrite(&h, sizeof(h), 1, F.f) != 1) return fail(FNR_ERR_IO, "write failed: %s", path);
@@ -540,7 +635,10 @@ fnr_status fnr_cache_load(fnr_context *ctx, const char *path, fnr_stream_t strea
     if (h.version != kFileVersion || h.header_bytes != sizeof(FileHeader))
         return fail(FNR_ERR_IO, "%s: format version %u is not supported", path, h.version);
     if (!desc_valid(&h.desc)) return fail(FNR_ERR_IO, "%s: invalid cache descriptor", path);
-    const Layout L = layout_of(&h.desc);
+    const bool bricks = h.desc.layout == FNR_LAYOUT_BRICKS;
+    if (bricks && h.n_bricks > (uint64_t(h.desc.k) * h.desc.k * h.desc.k))
+        return fail(FNR_ERR_IO, "%s: brick count out of range", path);
+    const Layout L = layout_of(&h.desc, bricks ? int64_t(h.n_bricks) : -1);
     if (h.footprint != L.total)
         return fail(FNR_ERR_IO, "%s: footprint %llu does not match the descriptor's %llu", path,
                     (unsigned long long)h.footprint, (unsigned long long)L.total);
@@ -552,6 +650,7 @@ fnr_status fnr_cache_load(fnr_context *ctx, const char *path, fnr_stream_t strea
     fnr_cache *c = new fnr_cache();
     c->desc = h.desc;
     c->footprint = L.total;
+    c->n_bricks = bricks ? h.n_bricks : 0;
     c->ctx = ctx;
     fnr_status st = FNR_OK;
     if ((e = cudaMalloc(&c->base, L.total)) != cudaSuccess) {
@@ -603,6 +702,10 @@ fnr_status fnr_cache_get_layout(const fnr_cache *c, fnr_cache_layout *out) {
     out->occupancy_dev = v.occ;
     out->record_stride = v.rec_stride;
     out->occupancy_brick = 1 << v.occ_shift;
+    out->layout = v.layout;
+    out->reserved1 = 0;
+    out->page_table_dev = v.page;
+    out->n_bricks = c->n_bricks;
     out->footprint = c->footprint;
     return FNR_OK;
 }

@@ -22,8 +22,10 @@ struct CacheView {
     const float *qp;      // [l] azimuth-key boundaries
     const float *scales;  // FP8: [1 + 3D]
     const uint32_t *occ;  // brick occupancy bits, brick (bz * occ_dim + by) * occ_dim + bx
+    const int32_t *page;  // FNR_LAYOUT_BRICKS: brick -> pool slot (-1 empty); sigma / uvw are the pools
     int32_t occ_shift;    // log2 of the brick side in cells
     int32_t occ_dim;      // bricks per axis, ceil(k / 2^occ_shift)
+    int32_t layout;       // FNR_LAYOUT_*
     float bmin[3];
     float scale[3];       // binary32(k / (bmax - bmin)) per axis
     float kf;             // (float)k
@@ -95,6 +97,10 @@ size_t elem_bytes(int prec);
 
 // Launchers (march.cu / quant.cu). Return cudaError_t of the launch.
 cudaError_t launch_march(const MarchArgs &a, cudaStream_t s);
+// Dense cache -> brick pools: pool slot s holds brick slot_brick[s] (k^3 grid, bricks of 2^shift cells).
+cudaError_t launch_gather_bricks(const void *sigma, const char *uvw, void *sigma_pool, char *uvw_pool,
+                                 const int32_t *slot_brick, int64_t n_bricks, int k, int shift, int dim,
+                                 int s_sigma, int rec_stride, cudaStream_t s);
 cudaError_t launch_convert_sigma(const float *in, void *out, int64_t n, int prec, const float *scale,
                                  cudaStream_t s);
 cudaError_t launch_convert_uvw(const float *in, char *out, int64_t n_cells, int D, int prec, int rec_stride,
@@ -123,6 +129,7 @@ struct fnr_cache {
     void *base = nullptr;
     bool owned = true;
     uint64_t footprint = 0;
+    uint64_t n_bricks = 0;  // FNR_LAYOUT_BRICKS: bricks in the pools
     fnr::CacheView view;
     std::atomic<int> inflight{0};
     fnr_context *ctx = nullptr;

@@ -338,6 +338,24 @@ struct RaySetup {
         return (iz * c.k + iy) * c.k + ix;
     }
 
+    // Brick and brick-local index ((z mod B) B + (y mod B)) B + (x mod B) of
+    // sample fi; false if the sample is outside the box (checked when `check`).
+    __device__ __forceinline__ bool cell_bl(const CacheView &c, float fi, int &brick, int &local, bool check) const {
+        const int ix = __float2int_rd(__fmaf_rn(fi, e[0], f[0]));
+        const int iy = __float2int_rd(__fmaf_rn(fi, e[1], f[1]));
+        const int iz = __float2int_rd(__fmaf_rn(fi, e[2], f[2]));
+        if (check) {
+            const unsigned int ku = static_cast<unsigned int>(c.k);
+            if (!(static_cast<unsigned int>(ix) < ku && static_cast<unsigned int>(iy) < ku &&
+                  static_cast<unsigned int>(iz) < ku))
+                return false;
+        }
+        const int sh = c.occ_shift, m = (1 << sh) - 1;
+        brick = ((iz >> sh) * c.occ_dim + (iy >> sh)) * c.occ_dim + (ix >> sh);
+        local = ((((iz & m) << sh) | (iy & m)) << sh) | (ix & m);
+        return true;
+    }
+
     // The same two with the sample's occupancy brick (meaningful when inside).
     __device__ __forceinline__ int cell_of_b(const CacheView &c, float fi, int &brick) const {
         const int ix = __float2int_rd(__fmaf_rn(fi, e[0], f[0]));
@@ -417,7 +435,10 @@ struct WarpQueue {
 // SKIP (FNR_RENDER_SKIP_EMPTY): a sample in a brick without stored density is
 // known to be empty, so only samples in occupied bricks load their density; the
 // lookup counter counts those loads. Everything else is unchanged.
-template <int PREC, int D, bool SKIP>
+// BRICKS (FNR_LAYOUT_BRICKS, implies SKIP): densities and records live in brick
+// pools; an occupied sample's pool index comes from the page table, and the
+// queue carries pool indices instead of cells.
+template <int PREC, int D, bool SKIP, bool BRICKS = false>
 __device__ __forceinline__ void march_tile_queued(const CacheView &c, const RenderConst &r, const FrameDesc &F,
                                                   int px, int py, bool active, WarpQueue<D> &q) {
     constexpr unsigned FULL = 0xffffffffu;
@@ -506,7 +527,27 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
         // Groups certainly inside the box for every lane still marching take the
         // path without per-sample range tests (warp-uniform choice).
         const bool inside = done || (i0 >= R.in_lo && i0 + kUnroll <= R.in_hi);
-        if constexpr (SKIP) {
+        if constexpr (BRICKS) {
+            // pool index of each sample in an occupied brick (page table read only for those)
+            const bool all_in = __all_sync(FULL, inside);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                int br = 0, loc = 0;
+                const bool in = all_in ? (R.cell_bl(c, fi, br, loc, false), !done)
+                                       : (((vis >> u) & 1u) && R.cell_bl(c, fi, br, loc, true));
+                const unsigned ob = in ? brick_occupied(c, br) : 0u;
+                in_m |= ob << u;
+                cell[u] = ob ? ((__ldg(c.page + br) << (3 * c.occ_shift)) | loc) : -1;
+                fi = __fadd_rn(fi, 1.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                sg[u] = ((in_m >> u) & 1u) ? load_sigma<PREC>(c, cell[u], R.sigma_scale) : 0.0f;
+            if constexpr (!kMaxTest) {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) occ_m |= (sg[u] > 0.0f ? 1u : 0u) << u;
+            }
+        } else if constexpr (SKIP) {
             // density lookups only in occupied bricks: in_m = the lookups made
             if (__all_sync(FULL, inside)) {
 #pragma unroll
@@ -563,7 +604,9 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
         if (cells_out) {
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u)
-                if ((vis >> u) & 1u) cells_out[i0 + u] = cell[u];  // past termination: overwritten by -2 below
+                if ((vis >> u) & 1u)  // past termination: overwritten by -2 below
+                    cells_out[i0 + u] =
+                        BRICKS ? R.cell_of(c, __fadd_rn(static_cast<float>(i0 + u), 0.5f)) : cell[u];
         }
         if constexpr (kMaxTest) {
             // Any occupied sample in the warp? Densities are finite and >= 0 (negative

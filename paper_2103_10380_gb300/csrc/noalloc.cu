@@ -128,6 +128,8 @@ extern "C" fnr_status fnr_render_noalloc(const fnr_cache *cache, const fnr_camer
     RenderConst rc;
     fnr_status st = make_render_const(params, &rc);
     if (st != FNR_OK) return st;
+    if (cache->view.layout == FNR_LAYOUT_BRICKS)
+        return fail(FNR_ERR_UNSUPPORTED, "fnr_render_noalloc reads dense caches (FNR_LAYOUT_DENSE)");
     if (rc.flags & FNR_RENDER_SKIP_EMPTY)
         return fail(FNR_ERR_UNSUPPORTED, "fnr_render_noalloc renders the plain path only (no FNR_RENDER_SKIP_EMPTY)");
     for (int i = 0; i < n_cams; ++i)

@@ -118,7 +118,41 @@ __global__ void occupancy_kernel(const CacheView v, uint32_t *__restrict__ words
     }
 }
 
+// One pool element per thread: cell (x, y, z) of brick slot_brick[slot] at
+// pool index slot B^3 + (lz B + ly) B + lx; cells past the grid edge are 0.
+__global__ void gather_bricks_kernel(const char *__restrict__ sigma, const char *__restrict__ uvw,
+                                     char *__restrict__ sigma_pool, char *__restrict__ uvw_pool,
+                                     const int32_t *__restrict__ slot_brick, int64_t n_elems, int k, int shift,
+                                     int dim, int s_sigma, int rec_stride) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int mask = (1 << shift) - 1;
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n_elems; e += stride) {
+        const int64_t slot = e >> (3 * shift);
+        const int local = static_cast<int>(e & ((int64_t(1) << (3 * shift)) - 1));
+        const int brick = slot_brick[slot];
+        const int bx = brick % dim, by = (brick / dim) % dim, bz = brick / (dim * dim);
+        const int x = (bx << shift) + (local & mask), y = (by << shift) + ((local >> shift) & mask),
+                  z = (bz << shift) + (local >> (2 * shift));
+        const bool in = x < k && y < k && z < k;
+        const int64_t cell = in ? (static_cast<int64_t>(z) * k + y) * k + x : 0;
+        for (int b = 0; b < s_sigma; ++b) sigma_pool[e * s_sigma + b] = in ? sigma[cell * s_sigma + b] : char(0);
+        const uint64_t *src = reinterpret_cast<const uint64_t *>(uvw + cell * rec_stride);
+        uint64_t *dst = reinterpret_cast<uint64_t *>(uvw_pool + e * rec_stride);
+        for (int w = 0; w < rec_stride / 8; ++w) dst[w] = in ? src[w] : 0ull;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_gather_bricks(const void *sigma, const char *uvw, void *sigma_pool, char *uvw_pool,
+                                 const int32_t *slot_brick, int64_t n_bricks, int k, int shift, int dim,
+                                 int s_sigma, int rec_stride, cudaStream_t s) {
+    const int64_t n = n_bricks << (3 * shift);
+    gather_bricks_kernel<<<grid_for(n, 256), 256, 0, s>>>(static_cast<const char *>(sigma), uvw,
+                                                          static_cast<char *>(sigma_pool), uvw_pool, slot_brick, n, k,
+                                                          shift, dim, s_sigma, rec_stride);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_occupancy(const CacheView &v, uint32_t *words, cudaStream_t s) {
     const int64_t n = static_cast<int64_t>(v.k) * v.k * v.k;

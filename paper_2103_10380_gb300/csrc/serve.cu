@@ -552,6 +552,8 @@ fnr_status fnr_submit(fnr_context *ctx, const fnr_request *req, uint64_t *ticket
     if (st != FNR_OK) return st;
     if ((st = check_camera(&req->camera)) != FNR_OK) return st;
     const int D = req->cache->desc.D;
+    if (req->cache->view.layout == FNR_LAYOUT_BRICKS)
+        return fail(FNR_ERR_UNSUPPORTED, "served rendering reads dense caches (FNR_LAYOUT_DENSE)");
     r.key = serve_key(req->cache->desc.pos_precision, D, (r.rc.flags & FNR_RENDER_SKIP_EMPTY) != 0u);
     if (!serve_fn(r.key))
         return fail(FNR_ERR_UNSUPPORTED, "served rendering supports D in {1,2,3,4,6,8,12,16}, got %d", D);
