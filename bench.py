@@ -120,8 +120,8 @@ def algorithmic_bytes(stats: np.ndarray, D: int, s_sigma: int, s_uvw: int, s_bet
 
 # DRAM bytes (read + write) of one plain FP32 march launch of the default workload, from one ncu capture
 # (profiles/march_fp32_k512_800x800_traffic.md); reported only while the kernel sources are unchanged.
-MARCH_TRAFFIC = {"sources_sha256": "bbb3c5522a5cb752ab34ca09d3adddca1dfc810b2f6208cb0b4ebc0ada4981b8",
-                 "bytes_per_launch": 334.1e6, "k": 512}
+MARCH_TRAFFIC = {"sources_sha256": "83ccd09f3c5fa14a8ab6931507d9ca2b751c8d1516f7bde96ac1fa90711942b1",
+                 "bytes_per_launch": 334.0e6, "k": 512}
 MARCH_SOURCES = ("march_device.cuh", "march.cu", "fnr_internal.h")
 
 
