@@ -41,7 +41,7 @@ int rec_stride_bytes(int prec, int D) {
 static uint64_t align256(uint64_t v) { return (v + 255u) & ~uint64_t(255u); }
 
 struct Layout {
-    uint64_t off_sigma, off_uvw, off_beta, off_ct, off_qp, off_scales, off_occ, off_page, total;
+    uint64_t off_sigma, off_uvw, off_beta, off_ct, off_qp, off_scales, off_occ, off_page, off_rank, total;
     int rec_stride;
 };
 
@@ -103,6 +103,8 @@ static Layout layout_of(const fnr_cache_desc *d, int64_t n_bricks = -1) {
     off = align256(off + occupancy_words(d) * 4);
     L.off_page = off;
     if (bricks) off = align256(off + nb * nb * nb * 4);
+    L.off_rank = off;
+    if (bricks) off = align256(off + occupancy_words(d) * 4);
     L.total = off;
     return L;
 }
@@ -236,6 +238,7 @@ static void fill_view(fnr_cache *c, const Layout &L) {
     v.occ = reinterpret_cast<const uint32_t *>(base + L.off_occ);
     v.layout = c->n_bricks > 0 || d.layout == FNR_LAYOUT_BRICKS ? FNR_LAYOUT_BRICKS : FNR_LAYOUT_DENSE;
     v.page = v.layout == FNR_LAYOUT_BRICKS ? reinterpret_cast<const int32_t *>(base + L.off_page) : nullptr;
+    v.rank = v.layout == FNR_LAYOUT_BRICKS ? reinterpret_cast<const uint32_t *>(base + L.off_rank) : nullptr;
     v.occ_shift = occupancy_shift(&d);
     v.occ_dim = (d.k + (1 << v.occ_shift) - 1) >> v.occ_shift;
     for (int a = 0; a < 3; ++a) {
@@ -397,11 +400,14 @@ static fnr_status make_bricks(fnr_context *ctx, const fnr_cache *dense, const fn
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(e, "occupancy read-back");
     std::vector<int32_t> page(size_t(nb3), -1), slot_brick;
-    for (int64_t b = 0; b < nb3; ++b)
+    std::vector<uint32_t> rank(words.size());
+    for (int64_t b = 0; b < nb3; ++b) {
+        if ((b & 31) == 0) rank[size_t(b >> 5)] = uint32_t(slot_brick.size());
         if ((words[size_t(b >> 5)] >> (b & 31)) & 1u) {
             page[size_t(b)] = int32_t(slot_brick.size());
             slot_brick.push_back(int32_t(b));
         }
+    }
     const int64_t n_bricks = int64_t(slot_brick.size());
     const Layout L = layout_of(desc, n_bricks);
     const Layout LD = layout_of(&dense->desc);
@@ -428,6 +434,8 @@ static fnr_status make_bricks(fnr_context *ctx, const fnr_cache *dense, const fn
         ((n_bricks > 0 && (e = cudaMemcpyAsync(slots.p, slot_brick.data(), size_t(n_bricks) * 4,
                                                cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
          (e = cudaMemcpyAsync(base + L.off_page, page.data(), size_t(nb3) * 4, cudaMemcpyHostToDevice, s)) !=
+             cudaSuccess ||
+         (e = cudaMemcpyAsync(base + L.off_rank, rank.data(), rank.size() * 4, cudaMemcpyHostToDevice, s)) !=
              cudaSuccess ||
          (e = cudaMemcpyAsync(base + L.off_beta, dbase + LD.off_beta, L.off_page - L.off_beta,
                               cudaMemcpyDeviceToDevice, s)) != cudaSuccess))

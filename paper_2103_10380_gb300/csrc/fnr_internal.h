@@ -23,6 +23,7 @@ struct CacheView {
     const float *scales;  // FP8: [1 + 3D]
     const uint32_t *occ;  // brick occupancy bits, brick (bz * occ_dim + by) * occ_dim + bx
     const int32_t *page;  // FNR_LAYOUT_BRICKS: brick -> pool slot (-1 empty); sigma / uvw are the pools
+    const uint32_t *rank; // FNR_LAYOUT_BRICKS: set occupancy bits in the words before each word
     int32_t occ_shift;    // log2 of the brick side in cells
     int32_t occ_dim;      // bricks per axis, ceil(k / 2^occ_shift)
     int32_t layout;       // FNR_LAYOUT_*

@@ -436,8 +436,8 @@ struct WarpQueue {
 // known to be empty, so only samples in occupied bricks load their density; the
 // lookup counter counts those loads. Everything else is unchanged.
 // BRICKS (FNR_LAYOUT_BRICKS, implies SKIP): densities and records live in brick
-// pools; an occupied sample's pool index comes from the page table, and the
-// queue carries pool indices instead of cells.
+// pools in brick-index order; an occupied sample's pool slot is the brick's rank
+// among the occupied bricks, and the queue carries pool indices instead of cells.
 template <int PREC, int D, bool SKIP, bool BRICKS = false>
 __device__ __forceinline__ void march_tile_queued(const CacheView &c, const RenderConst &r, const FrameDesc &F,
                                                   int px, int py, bool active, WarpQueue<D> &q) {
@@ -528,17 +528,43 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
         // path without per-sample range tests (warp-uniform choice).
         const bool inside = done || (i0 >= R.in_lo && i0 + kUnroll <= R.in_hi);
         if constexpr (BRICKS) {
-            // pool index of each sample in an occupied brick (page table read only for those)
-            const bool all_in = __all_sync(FULL, inside);
+            // First the occupancy bits, exactly as the dense skip path; then, only if some lane
+            // of the warp has a sample in an occupied brick, those samples' pool indices: the
+            // brick's slot is its rank among the occupied bricks (a per-word prefix count plus a
+            // popcount, both from L1-resident arrays) and the cell's brick-local index.
+            const float fi0 = fi;
+            if (__all_sync(FULL, inside)) {
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                int br = 0, loc = 0;
-                const bool in = all_in ? (R.cell_bl(c, fi, br, loc, false), !done)
-                                       : (((vis >> u) & 1u) && R.cell_bl(c, fi, br, loc, true));
-                const unsigned ob = in ? brick_occupied(c, br) : 0u;
-                in_m |= ob << u;
-                cell[u] = ob ? ((__ldg(c.page + br) << (3 * c.occ_shift)) | loc) : -1;
-                fi = __fadd_rn(fi, 1.0f);
+                for (int u = 0; u < kUnroll; ++u) {
+                    int br;
+                    R.cell_inside_b(c, fi, br);
+                    in_m |= (!done ? brick_occupied(c, br) : 0u) << u;
+                    fi = __fadd_rn(fi, 1.0f);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    int br = 0;
+                    const bool in = ((vis >> u) & 1u) && R.cell_of_b(c, fi, br) >= 0;
+                    in_m |= (in ? brick_occupied(c, br) : 0u) << u;
+                    fi = __fadd_rn(fi, 1.0f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) cell[u] = -1;
+            if (__any_sync(FULL, in_m != 0u)) {
+                float fu = fi0;
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    if ((in_m >> u) & 1u) {
+                        int br, loc;
+                        R.cell_bl(c, fu, br, loc, false);
+                        const uint32_t wb = __ldg(c.occ + (br >> 5));
+                        const uint32_t slot = __ldg(c.rank + (br >> 5)) + __popc(wb & ((1u << (br & 31)) - 1u));
+                        cell[u] = static_cast<int>((slot << (3 * c.occ_shift)) | static_cast<uint32_t>(loc));
+                    }
+                    fu = __fadd_rn(fu, 1.0f);
+                }
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u)
