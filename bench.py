@@ -357,6 +357,54 @@ def cache_build(fnr, torch, ctx, k=512, l=512):
             "timing": "whole fnr_build_cache call (includes the cache allocation), best of 2"}
 
 
+def uncached_render(fnr, torch, dev, w, reps=3):
+    """The uncached render (the paper's "no cache" row): one 800x800 view, N=128, F_pos (8x256 + head, L=10)
+    at every inside sample and F_dir (4x128 + head, L=4) per ray on the tensor cores, random He-uniform
+    weights; the per-frame time of fnr_render_mlp (samples, both MLPs, compositing) and the MLP FLOPs."""
+    import scenegen
+    pos = scenegen.mlp_weights(0, scenegen.FPOS_DIMS_D8)
+    dirn = scenegen.mlp_weights(100, scenegen.FDIR_DIMS_D8)
+    devw = lambda L: [(torch.from_numpy(W.view(np.int16)).to(dev), torch.from_numpy(b).to(dev)) for W, b in L]
+    pl, dl = devw(pos), devw(dirn)
+    ctx = fnr.fnr_context_create(dev.index or 0, 0)
+    cam = w.cameras()[0]
+    npix = w.W * w.H
+    rgba = torch.empty(npix * 4, device=dev)
+    stats = torch.empty(npix * 4, device=dev, dtype=torch.int32)
+    params = fnr.make_params(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg)
+    fnr.fnr_render_mlp(ctx, pl, dl, w.D, cam, params, rgba, stats)
+    torch.cuda.synchronize(dev)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fnr.fnr_render_mlp(ctx, pl, dl, w.D, cam, params, rgba, None)
+        torch.cuda.synchronize(dev)
+        times.append(time.perf_counter() - t0)
+    fnr.fnr_context_destroy(ctx)
+    # every inside sample is evaluated: count them with the oracle's sample positions (same binary32 rule)
+    import ctypes
+    import oracle
+    py, px = np.meshgrid(np.arange(w.H, dtype=np.int32), np.arange(w.W, dtype=np.int32), indexing="ij")
+    px, py = np.ascontiguousarray(px.reshape(-1)), np.ascontiguousarray(py.reshape(-1))
+    op = oracle.params_struct(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg)
+    pts = np.zeros((npix, w.n_samples, 3), np.float32)
+    inside = np.zeros((npix, w.n_samples), np.uint8)
+    dirs = np.zeros((npix, 3), np.float32)
+    lo, hi = np.full(3, -1.5, np.float32), np.full(3, 1.5, np.float32)
+    oracle.lib().orc_mlp_samples(ctypes.byref(oracle.camera_struct(cam)), ctypes.byref(op), lo.ctypes.data,
+                                 hi.ctypes.data, npix, px.ctypes.data, py.ctypes.data, pts.ctypes.data,
+                                 inside.ctypes.data, dirs.ctypes.data)
+    n_pts = int(inside.sum())
+    fl = lambda dims: 2 * sum(a * b for a, b in zip(dims[:-1], dims[1:]))
+    flops = fl(scenegen.FPOS_DIMS_D8) * n_pts + fl(scenegen.FDIR_DIMS_D8) * npix
+    dt = min(times)
+    return {"workload": f"{w.W}x{w.H}, N={w.n_samples}, random He-uniform F_pos / F_dir", "frame_ms": dt * 1e3,
+            "mrays_per_s": npix / dt / 1e6, "inside_samples": n_pts, "mlp_flops": flops,
+            "mlp_tflops": flops / dt / 1e12,
+            "timing": "whole fnr_render_mlp call (allocation, samples, F_pos over every inside sample, F_dir per "
+                      "ray, compositing), best of %d" % reps}
+
+
 RATES = (50.0, 100.0, 200.0, 400.0)
 
 
@@ -749,6 +797,7 @@ def run_fnr(args):
             out["serving"] = serving_config(fnr, torch, dev, w, sig, uvw, beta, args.serve_seconds)
             out["precision_k1024"] = precision_config(fnr, torch, dev)
             out["cache_build"] = cache_build(fnr, torch, ctx)
+            out["uncached_render"] = uncached_render(fnr, torch, dev, w)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, sig, uvw, beta, cams, args.cpu_seconds)
         print(json.dumps(out), flush=True)

@@ -301,6 +301,23 @@ FNR_API fnr_status fnr_render(fnr_context *ctx, const fnr_cache *cache, const fn
                       int32_t *debug_cells_dev, fnr_stream_t stream);
 
 
+/* The uncached render ("no cache" in the paper's timings, Section 5): F_pos
+ * evaluated at every sample inside the box and F_dir at the ray direction on
+ * the tensor cores, then Eq. 5 and Eq. 1 exactly as fnr_render composites
+ * them. Samples: t_i = fma(i + 1/2, Delta, near) and p_a = fma(t_i, d_a, o_a)
+ * in binary32 (d, o from the fixed ray sequence); p is inside iff
+ * bmin_a <= p_a < bmax_a on every axis. F_pos reads the raw position (its
+ * positional encoding as for the cache build); sigma = ReLU(output 0), u_i,
+ * v_i, w_i = outputs 1..3D; F_dir reads the unit direction; beta = outputs
+ * 0..D-1. One view per call; device temporaries are allocated per call and
+ * charged to the budget. Stats: n_lookups = inside samples up to termination,
+ * n_occupied = those with sigma > 0, dir_cell = -1. Errors: INVALID_ARG,
+ * UNSUPPORTED, BUDGET, CUDA, DEVICE. */
+FNR_API fnr_status fnr_render_mlp(fnr_context *ctx, const fnr_mlp *pos_mlp, const fnr_mlp *dir_mlp, int32_t D,
+                                  const float *bmin, const float *bmax, const fnr_camera *cam,
+                                  const fnr_render_params *params, float *rgba_dev, fnr_ray_stats *stats_dev,
+                                  fnr_stream_t stream);
+
 /* ------------------------------------------------------------------ serving */
 /* A request for one view (Section 4's per-view render, served). The request
  * is copied at submit; rgba_dev / stats_dev stay caller-owned and must stay

@@ -9,6 +9,7 @@ stated in oracle.c.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 
@@ -95,6 +96,8 @@ def lib():
         L.orc_table_field.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P]
         L.orc_beta_bilinear.argtypes = [P, P, P]
         L.orc_beta_bilinear.restype = None
+        L.orc_mlp_samples.argtypes = [P, P, P, P, ctypes.c_int64, P, P, P, P, P]
+        L.orc_mlp_samples.restype = None
         L.orc_table_field.restype = None
         _lib = L
     return _lib
@@ -272,6 +275,58 @@ def beta_bilinear(cache: Cache, d) -> np.ndarray:
     out = np.zeros(cache.D)
     lib().orc_beta_bilinear(ctypes.byref(cache._s), _p(d), _p(out))
     return out
+
+
+def render_mlp_pixels(pos_layers, dir_layers, D, cam: dict, params: _Params, px, py, pos_freqs=10, dir_freqs=4,
+                      bmin=(-1.5, -1.5, -1.5), bmax=(1.5, 1.5, 1.5), round_bf16=True, nthreads=None):
+    """The uncached render of listed pixels (FP64): F_pos (layers [(W FP64, b FP64)]) at every sample inside
+    the box (binary32 positions, orc_mlp_samples), F_dir at the ray direction, then Eq. 5 with the sigmoid
+    and Eq. 1 with the exact integer termination on sigma rounded to binary32 (the width the renderer
+    keeps it in). round_bf16: the activations between layers (and the encoded input) are rounded to bf16 as
+    the tensor cores see them. Returns (rgba [n,4] f64, stats [n,4] i32: n_steps, n_lookups, n_occupied, -1)."""
+    px = np.ascontiguousarray(px, dtype=np.int32).reshape(-1)
+    py = np.ascontiguousarray(py, dtype=np.int32).reshape(-1)
+    n, N = px.size, params.N
+    pts = np.zeros((n, N, 3), np.float32)
+    inside = np.zeros((n, N), np.uint8)
+    dirs = np.zeros((n, 3), np.float32)
+    lo, hi = np.asarray(bmin, np.float32), np.asarray(bmax, np.float32)
+    cs = camera_struct(cam)
+    lib().orc_mlp_samples(ctypes.byref(cs), ctypes.byref(params), _p(lo), _p(hi), n, _p(px), _p(py), _p(pts),
+                          _p(inside), _p(dirs))
+    mask = inside.astype(bool)
+    out = mlp_eval(pos_layers, pts[mask].astype(np.float64), pos_freqs, round_bf16, nthreads)
+    beta = mlp_eval(dir_layers, dirs.astype(np.float64), dir_freqs, round_bf16, nthreads)[:, :D]
+    dtv = float(dt(params.t_near, params.t_far, N))
+    sthr = s_thr(params.t_thr, dtv) if params.t_thr > 0 else (1 << 63) - 1
+    rgba = np.zeros((n, 4))
+    stats = np.zeros((n, 4), np.int32)
+    j = 0
+    for r in range(n):
+        T, C, S = 1.0, np.zeros(3), 0
+        n_steps, n_look, n_occ = N, 0, 0
+        idx = np.flatnonzero(mask[r])
+        for i in idx:
+            o = out[j + n_look]
+            n_look += 1
+            sg = max(o[0], 0.0)
+            if not sg > 0.0:
+                continue
+            n_occ += 1
+            x = beta[r] @ o[1:1 + 3 * D].reshape(3, D).T  # Eq. 5: x_ch = sum_i beta_i u_ch,i
+            col = x if params.act == ACT_IDENTITY else 1.0 / (1.0 + np.exp(-x))
+            od = sg * dtv
+            C += T * (-math.expm1(-od)) * col  # Eq. 1
+            T *= math.exp(-od)
+            S = min(S + fix(float(np.float32(sg))), (1 << 63) - 1)
+            if S >= sthr:
+                n_steps = int(i) + 1
+                break
+        j += int(mask[r].sum())
+        rgba[r, :3] = C + T * np.asarray(params.bg[:], np.float64)
+        rgba[r, 3] = 1.0 - T
+        stats[r] = (n_steps, n_look, n_occ, -1)
+    return rgba, stats
 
 
 def dir_cell(l: int, d) -> tuple:

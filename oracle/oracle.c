@@ -503,6 +503,31 @@ int orc_render_pixels(const orc_cache *c, const orc_camera *cam, const orc_param
     return 0;
 }
 
+/* ------------------------------------------------------------ uncached samples */
+/* Sample positions of the uncached render (F_pos evaluated at the samples
+ * themselves rather than at cell centres): t_i = fma(i + 1/2, Delta, near) and
+ * p_a = fma(t_i, d_a, o_a) in binary32, inside iff bmin_a <= p_a < bmax_a on
+ * every axis. Per pixel: points [N][3], inside [N] (0 / 1), the unit direction. */
+void orc_mlp_samples(const orc_camera *cam, const orc_params *p, const float *bmin, const float *bmax, int64_t n,
+                     const int32_t *px, const int32_t *py, float *points, uint8_t *inside, float *dirs) {
+    const float dt = orc_dt(p->t_near, p->t_far, p->N);
+    for (int64_t r = 0; r < n; ++r) {
+        float d[3], o[3];
+        orc_ray(cam, px[r], py[r], d, o);
+        for (int a = 0; a < 3; ++a) dirs[3 * r + a] = d[a];
+        for (int i = 0; i < p->N; ++i) {
+            const float t = fmaf((float)i + 0.5f, dt, p->t_near);
+            int in = 1;
+            for (int a = 0; a < 3; ++a) {
+                const float v = fmaf(t, d[a], o[a]);
+                points[(r * p->N + i) * 3 + a] = v;
+                if (!(v >= bmin[a] && v < bmax[a])) in = 0;
+            }
+            inside[r * p->N + i] = (uint8_t)in;
+        }
+    }
+}
+
 /* ------------------------------------------------------------ FP64 geometry */
 /* The same sample positions with every step in FP64 and libm acos/atan2 for the
  * direction, to cross-check the binary32 index decisions: for each sample,

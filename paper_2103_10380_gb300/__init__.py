@@ -125,6 +125,8 @@ SIGNATURES = {
     "fnr_cache_free": ([_P, _P], ctypes.c_int32),
     "fnr_cache_get_layout": ([_P, ctypes.POINTER(fnr_cache_layout)], ctypes.c_int32),
     "fnr_cache_save": ([_P, ctypes.c_char_p], ctypes.c_int32),
+    "fnr_render_mlp": ([_P, _P, _P, ctypes.c_int32, _P, _P, ctypes.POINTER(fnr_camera),
+                        ctypes.POINTER(fnr_render_params), _P, _P, _P], ctypes.c_int32),
     "fnr_cache_load": ([_P, ctypes.c_char_p, _P, ctypes.POINTER(_P)], ctypes.c_int32),
     "fnr_render": ([_P, _P, ctypes.POINTER(fnr_camera), ctypes.c_int32, ctypes.POINTER(fnr_render_params), _P, _P,
                     _P, _P], ctypes.c_int32),
@@ -253,6 +255,20 @@ def fnr_build_cache_mlp(ctx: int, desc: fnr_cache_desc, pos_layers, dir_layers, 
     check(lib().fnr_build_cache(ctx, ctypes.byref(desc), ctypes.byref(src), _stream_handle(stream),
                                 ctypes.byref(out)))
     return out.value
+
+
+def fnr_render_mlp(ctx: int, pos_layers, dir_layers, D: int, cam, params: fnr_render_params, rgba, stats=None,
+                   bmin=(-1.5, -1.5, -1.5), bmax=(1.5, 1.5, 1.5), pos_freqs: int = 10, dir_freqs: int = 4,
+                   stream=None):
+    """The uncached render of one view: F_pos at every inside sample, F_dir per ray, Eq. 5 + Eq. 1."""
+    pm, dm = make_mlp(pos_layers, pos_freqs), make_mlp(dir_layers, dir_freqs)
+    c = cam if isinstance(cam, fnr_camera) else make_camera(cam)
+    lo = (ctypes.c_float * 3)(*[float(v) for v in bmin])
+    hi = (ctypes.c_float * 3)(*[float(v) for v in bmax])
+    assert rgba.is_cuda and rgba.is_contiguous() and rgba.numel() >= 4 * c.width * c.height
+    check(lib().fnr_render_mlp(ctx, ctypes.addressof(pm), ctypes.addressof(dm), int(D), ctypes.addressof(lo),
+                               ctypes.addressof(hi), ctypes.byref(c), ctypes.byref(params), rgba.data_ptr(),
+                               None if stats is None else stats.data_ptr(), _stream_handle(stream)))
 
 
 def fnr_cache_free(ctx: int, cache: int):

@@ -120,6 +120,8 @@ void server_stop(fnr_context *ctx);
 
 // mlp.cu: tensor-core evaluation of F_pos (mode 0) / F_dir (mode 1) into a cache.
 fnr_status check_mlp(const fnr_mlp *m, int n_out_min, const char *name);
+fnr_status run_mlp_points(const fnr_mlp *m, const float *points, long long n, float *out, int out_stride,
+                          bool relu0, int num_sms, cudaStream_t s);
 fnr_status run_mlp(const fnr_mlp *m, int mode, const fnr_cache_desc &d, const CacheView &v, int num_sms,
                    cudaStream_t s);
 

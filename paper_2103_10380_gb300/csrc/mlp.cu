@@ -111,6 +111,11 @@ struct MlpArgs {
     int rec_stride, prec, D;
     void *beta_out;    // mode 1
     int dprec;
+    // mode 2: F evaluated at listed points (positions, or unit directions for F_dir); the head's
+    // first out_stride outputs go to out[p * out_stride + c] in FP32 (channel 0 through ReLU if relu0)
+    const float *points;  // [n_points][3]
+    float *out;
+    int out_stride, relu0;
     int *err;
 };
 
@@ -253,7 +258,11 @@ __device__ __forceinline__ void encode_point(const MlpArgs &A, long long p, int 
     float x[3] = {0.0f, 0.0f, 0.0f};
     const bool valid = p < A.n_points;
     if (valid) {
-        if (A.mode == 0) {
+        if (A.mode == 2) {
+            x[0] = A.points[3 * p];
+            x[1] = A.points[3 * p + 1];
+            x[2] = A.points[3 * p + 2];
+        } else if (A.mode == 0) {
             const long long kk = A.k;
             const int ix = int(p % kk), iy = int((p / kk) % kk), iz = int(p / (kk * kk));
             x[0] = fmaf(float(ix) + 0.5f, A.h[0], A.bmin[0]);
@@ -481,7 +490,10 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                             for (int u = 0; u < 16; ++u) {
                                 const int c = c0 + u;
                                 const float o = v[u];
-                                if (A.mode == 0) {
+                                if (A.mode == 2) {
+                                    if (c < A.out_stride)
+                                        A.out[p * A.out_stride + c] = (c == 0 && A.relu0) ? fmaxf(o, 0.0f) : o;
+                                } else if (A.mode == 0) {
                                     if (c == 0) {
                                         const float sg = fmaxf(o, 0.0f);
                                         if (A.prec == FNR_PREC_FP16)
@@ -595,9 +607,11 @@ fnr_status check_mlp(const fnr_mlp *m, int n_out_min, const char *name) {
     return FNR_OK;
 }
 
-// Evaluate one MLP over its grid into the cache (mode 0: F_pos, 1: F_dir).
-fnr_status run_mlp(const fnr_mlp *m, int mode, const fnr_cache_desc &d, const CacheView &v, int num_sms,
-                   cudaStream_t s) {
+namespace {
+
+// Lay out the weights and biases of m, fill the layer table of A, launch the
+// kernel on the mode-specific arguments already in A, and wait for it.
+fnr_status mlp_launch(const fnr_mlp *m, MlpArgs &A, int num_sms, cudaStream_t s) {
     struct Buf {
         void *p = nullptr;
         ~Buf() {
@@ -614,8 +628,6 @@ fnr_status run_mlp(const fnr_mlp *m, int mode, const fnr_cache_desc &d, const Ca
     if ((e = cudaMalloc(&bbuf.p, belems * 4)) != cudaSuccess) return cuda_fail(e, "MLP biases");
     if ((e = cudaMalloc(&ebuf.p, 4)) != cudaSuccess) return cuda_fail(e, "MLP error word");
     if ((e = cudaMemsetAsync(ebuf.p, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "memset");
-    MlpArgs A;
-    memset(&A, 0, sizeof(A));
     size_t wo = 0, bo = 0;
     for (int i = 0; i < m->n_layers; ++i) {
         const int K = m->dims[i], N = m->dims[i + 1], Kp = round64(K), Np = round16(N);
@@ -634,23 +646,9 @@ fnr_status run_mlp(const fnr_mlp *m, int mode, const fnr_cache_desc &d, const Ca
     A.bias = static_cast<const float *>(bbuf.p);
     A.n_bias = int(bo);
     A.n_layers = m->n_layers;
-    A.mode = mode;
     A.pe_freqs = m->pe_freqs;
-    A.k = d.k;
-    A.l = d.l;
-    for (int a = 0; a < 3; ++a) {
-        A.bmin[a] = d.bmin[a];
-        A.h[a] = static_cast<float>((static_cast<double>(d.bmax[a]) - d.bmin[a]) / d.k);
-    }
-    A.n_points = mode == 0 ? (long long)d.k * d.k * d.k : (long long)d.l * d.l;
-    A.sigma_out = const_cast<void *>(v.sigma);
-    A.uvw_out = const_cast<char *>(v.uvw);
-    A.rec_stride = v.rec_stride;
-    A.prec = d.pos_precision;
-    A.D = d.D;
-    A.beta_out = const_cast<void *>(v.beta);
-    A.dprec = d.dir_precision;
     A.err = static_cast<int *>(ebuf.p);
+    if (A.n_points <= 0) return FNR_OK;
     if ((e = cudaFuncSetAttribute(mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes))) !=
         cudaSuccess)
         return cuda_fail(e, "MLP smem attribute");
@@ -689,6 +687,46 @@ fnr_status run_mlp(const fnr_mlp *m, int mode, const fnr_cache_desc &d, const Ca
         return cuda_fail(e, "MLP sync");
     if (herr) return fail(FNR_ERR_DEVICE, "MLP kernel: an mbarrier wait ran out");
     return FNR_OK;
+}
+
+}  // namespace
+
+// Evaluate one MLP over its grid into the cache (mode 0: F_pos, 1: F_dir).
+fnr_status run_mlp(const fnr_mlp *m, int mode, const fnr_cache_desc &d, const CacheView &v, int num_sms,
+                   cudaStream_t s) {
+    MlpArgs A;
+    memset(&A, 0, sizeof(A));
+    A.mode = mode;
+    A.k = d.k;
+    A.l = d.l;
+    for (int a = 0; a < 3; ++a) {
+        A.bmin[a] = d.bmin[a];
+        A.h[a] = static_cast<float>((static_cast<double>(d.bmax[a]) - d.bmin[a]) / d.k);
+    }
+    A.n_points = mode == 0 ? (long long)d.k * d.k * d.k : (long long)d.l * d.l;
+    A.sigma_out = const_cast<void *>(v.sigma);
+    A.uvw_out = const_cast<char *>(v.uvw);
+    A.rec_stride = v.rec_stride;
+    A.prec = d.pos_precision;
+    A.D = d.D;
+    A.beta_out = const_cast<void *>(v.beta);
+    A.dprec = d.dir_precision;
+    return mlp_launch(m, A, num_sms, s);
+}
+
+// Evaluate one MLP at n listed points ([n][3] on the device): the first
+// out_stride head outputs of point p go to out[p * out_stride + c] in FP32.
+fnr_status run_mlp_points(const fnr_mlp *m, const float *points, long long n, float *out, int out_stride,
+                          bool relu0, int num_sms, cudaStream_t s) {
+    MlpArgs A;
+    memset(&A, 0, sizeof(A));
+    A.mode = 2;
+    A.n_points = n;
+    A.points = points;
+    A.out = out;
+    A.out_stride = out_stride;
+    A.relu0 = relu0 ? 1 : 0;
+    return mlp_launch(m, A, num_sms, s);
 }
 
 }  // namespace fnr
