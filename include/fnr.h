@@ -142,8 +142,9 @@ typedef struct {
  * supplementary cache sizes): only the occupancy bricks (B^3 cells, B =
  * occupancy_brick) holding a stored density > 0 keep their sigma and records,
  * in a pool of bricks reached through a page table of ceil(k / B)^3 entries.
- * Renders from a BRICKS cache have FNR_RENDER_SKIP_EMPTY semantics whether or
- * not the flag is set (an empty brick has no storage). */
+ * Renders from a BRICKS cache (fnr_render, fnr_submit) have
+ * FNR_RENDER_SKIP_EMPTY semantics whether or not the flag is set (an empty
+ * brick has no storage); fnr_render_noalloc reads dense caches only. */
 #define FNR_LAYOUT_DENSE 0
 #define FNR_LAYOUT_BRICKS 1
 

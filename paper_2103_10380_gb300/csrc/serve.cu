@@ -81,7 +81,7 @@ __device__ __forceinline__ int serve_frame_of(const ServeTable &tab, int nf, int
     return lo;
 }
 
-template <int PREC, int D, bool SKIP>
+template <int PREC, int D, bool SKIP, bool BRICKS>
 __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
     serve_kernel(const __grid_constant__ ServeTable tab, ServeScratch *scr, volatile uint32_t *done_flags) {
     constexpr int kWarps = FNR_BLOCK / 32;
@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
         int x0, y0;
         tile_origin(sf.f, lt, x0, y0);
         const int px = x0 + (lane & (kTileW - 1)), py = y0 + lane / kTileW;
-        dev::march_tile_queued<PREC, D, SKIP>(sf.c, sf.r, sf.f, px, py, px < sf.f.W && py < sf.f.H, queues[warp]);
+        dev::march_tile_queued<PREC, D, SKIP, BRICKS>(sf.c, sf.r, sf.f, px, py, px < sf.f.W && py < sf.f.H,
+                                                      queues[warp]);
     }
     __syncthreads();  // the block's outputs are written
     if (threadIdx.x == 0) {
@@ -122,38 +123,41 @@ __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
 
 using ServeFn = void (*)(const ServeTable, ServeScratch *, volatile uint32_t *);
 
-template <int PREC, bool SKIP>
+template <int PREC, bool SKIP, bool BRICKS>
 ServeFn serve_fn_p(int D) {
     switch (D) {
-        case 1: return serve_kernel<PREC, 1, SKIP>;
-        case 2: return serve_kernel<PREC, 2, SKIP>;
-        case 3: return serve_kernel<PREC, 3, SKIP>;
-        case 4: return serve_kernel<PREC, 4, SKIP>;
-        case 6: return serve_kernel<PREC, 6, SKIP>;
-        case 8: return serve_kernel<PREC, 8, SKIP>;
-        case 12: return serve_kernel<PREC, 12, SKIP>;
-        case 16: return serve_kernel<PREC, 16, SKIP>;
+        case 1: return serve_kernel<PREC, 1, SKIP, BRICKS>;
+        case 2: return serve_kernel<PREC, 2, SKIP, BRICKS>;
+        case 3: return serve_kernel<PREC, 3, SKIP, BRICKS>;
+        case 4: return serve_kernel<PREC, 4, SKIP, BRICKS>;
+        case 6: return serve_kernel<PREC, 6, SKIP, BRICKS>;
+        case 8: return serve_kernel<PREC, 8, SKIP, BRICKS>;
+        case 12: return serve_kernel<PREC, 12, SKIP, BRICKS>;
+        case 16: return serve_kernel<PREC, 16, SKIP, BRICKS>;
         default: return nullptr;
     }
 }
 
-template <bool SKIP>
+template <bool SKIP, bool BRICKS>
 ServeFn serve_fn_s(int prec, int D) {
     switch (prec) {
-        case FNR_PREC_FP32: return serve_fn_p<FNR_PREC_FP32, SKIP>(D);
-        case FNR_PREC_FP16: return serve_fn_p<FNR_PREC_FP16, SKIP>(D);
-        case FNR_PREC_FP8_E4M3: return serve_fn_p<FNR_PREC_FP8_E4M3, SKIP>(D);
+        case FNR_PREC_FP32: return serve_fn_p<FNR_PREC_FP32, SKIP, BRICKS>(D);
+        case FNR_PREC_FP16: return serve_fn_p<FNR_PREC_FP16, SKIP, BRICKS>(D);
+        case FNR_PREC_FP8_E4M3: return serve_fn_p<FNR_PREC_FP8_E4M3, SKIP, BRICKS>(D);
         default: return nullptr;
     }
 }
 
-// Kernel key of a batch: requests share a launch when precision, D and the
-// skip flag agree.
-int serve_key(int prec, int D, bool skip) { return (skip ? 128 : 0) + prec * 32 + D; }
+// Kernel key of a batch: requests share a launch when precision, D, the skip
+// flag and the cache layout agree (brick caches always skip).
+int serve_key(int prec, int D, bool skip, bool bricks) {
+    return (bricks ? 256 : 0) + ((skip || bricks) ? 128 : 0) + prec * 32 + D;
+}
 
 ServeFn serve_fn(int key) {
     const int prec = (key & 127) / 32, D = key % 32;
-    return key & 128 ? serve_fn_s<true>(prec, D) : serve_fn_s<false>(prec, D);
+    if (key & 256) return serve_fn_s<true, true>(prec, D);
+    return key & 128 ? serve_fn_s<true, false>(prec, D) : serve_fn_s<false, false>(prec, D);
 }
 
 uint64_t now_ns() {
@@ -552,9 +556,8 @@ fnr_status fnr_submit(fnr_context *ctx, const fnr_request *req, uint64_t *ticket
     if (st != FNR_OK) return st;
     if ((st = check_camera(&req->camera)) != FNR_OK) return st;
     const int D = req->cache->desc.D;
-    if (req->cache->view.layout == FNR_LAYOUT_BRICKS)
-        return fail(FNR_ERR_UNSUPPORTED, "served rendering reads dense caches (FNR_LAYOUT_DENSE)");
-    r.key = serve_key(req->cache->desc.pos_precision, D, (r.rc.flags & FNR_RENDER_SKIP_EMPTY) != 0u);
+    r.key = serve_key(req->cache->desc.pos_precision, D, (r.rc.flags & FNR_RENDER_SKIP_EMPTY) != 0u,
+                      req->cache->view.layout == FNR_LAYOUT_BRICKS);
     if (!serve_fn(r.key))
         return fail(FNR_ERR_UNSUPPORTED, "served rendering supports D in {1,2,3,4,6,8,12,16}, got %d", D);
     r.rays = int64_t(req->camera.width) * req->camera.height;

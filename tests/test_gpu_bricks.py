@@ -119,7 +119,7 @@ def test_bricks_match_dense(fnr, ctx, prec, dprec, brick):
 
 def test_bricks_scale_footprint_and_paths(fnr, ctx, tmp_path):
     """512^3 FP32: the brick cache is a fraction of the dense one, renders like the dense skip render,
-    survives save/load; the served and allocation-free paths refuse it."""
+    survives save/load and is served; the allocation-free path refuses it."""
     import torch
     w = scenegen.scale()
     sig, uvw = scenegen.fill_position_grid(w.scene, w.k)
@@ -148,9 +148,19 @@ def test_bricks_scale_footprint_and_paths(fnr, ctx, tmp_path):
         with pytest.raises(fnr.FnrError) as ei:
             fnr.fnr_render_noalloc(bricks, [cam], fnr.make_params(w.n_samples), out)
         assert ei.value.status == fnr.FNR_ERR_UNSUPPORTED
-        with pytest.raises(fnr.FnrError) as ei:
-            fnr.fnr_submit(ctx, fnr.make_request(bricks, cam, fnr.make_params(w.n_samples), out))
-        assert ei.value.status == fnr.FNR_ERR_UNSUPPORTED
+        # served: brick-cache requests (mixed with dense ones) equal fnr_render's output bit for bit
+        fnr.fnr_serve_start(ctx, n_slots=2, max_batch_requests=8, use_graphs=1)
+        reqs = []
+        for i, c in enumerate(scenegen.cameras(31, 6, 320, 200, hemisphere=True)):
+            cache_i = bricks if i % 2 == 0 else dense
+            o = torch.zeros(320 * 200 * 4, device="cuda")
+            st = torch.zeros(320 * 200 * 4, device="cuda", dtype=torch.int32)
+            reqs.append((fnr.fnr_submit(ctx, fnr.make_request(cache_i, c, ps, o, st)), cache_i, c, o, st))
+        for t, cache_i, c, o, st in reqs:
+            assert fnr.fnr_wait(ctx, t, 20000).status == fnr.FNR_OK
+            ref = render(fnr, ctx, cache_i, c, ps)
+            assert np.array_equal(o.cpu().numpy(), ref[0]) and np.array_equal(st.cpu().numpy(), ref[1])
+        fnr.fnr_serve_stop(ctx)
     finally:
         fnr.fnr_cache_free(ctx, dense)
         fnr.fnr_cache_free(ctx, bricks)
