@@ -175,3 +175,31 @@ def test_served_skip_requests(fnr, tiny_workload, tiny_arrays):
         fnr.fnr_cache_free(ctx, cache)
     finally:
         fnr.fnr_context_destroy(ctx)
+
+
+@pytest.mark.parametrize("D", [1, 3, 16])
+def test_component_counts_skip_bricks_bilinear(fnr, ctx, D):
+    """Odd record sizes with skipping, brick caches and the interpolated direction lookup."""
+    k, l = 24, 16
+    sc = scenegen.make_scene(7, n_spheres=6, n_shells=2, D=D, sh_degree=2)
+    sig, uvw = scenegen.fill_position_grid(sc, k)
+    beta = scenegen.direction_grid(sc, l)
+    cam = scenegen.cameras(3, 1, 40, 24)[0]
+    arrs = (sig.reshape(-1), uvw.reshape(-1), beta.reshape(-1))
+    for prec in (0, 1, 2):
+        dense = fnr.fnr_build_cache(ctx, fnr.make_desc(k, D, l, prec, 0, occupancy_brick=4), *arrs)
+        bricks = fnr.fnr_build_cache(ctx, fnr.make_desc(k, D, l, prec, 0, occupancy_brick=4,
+                                                        layout=fnr.FNR_LAYOUT_BRICKS), *arrs)
+        try:
+            oc = oracle.quantize_cache(k, D, l, sig, uvw, beta, prec, 0).set_occupancy(4)
+            for bil in (False, True):
+                p = fnr.make_params(32, t_thr=1e-3, skip_empty=True, dir_bilinear=bil)
+                got = render(fnr, ctx, dense, cam, p)
+                got_b = render(fnr, ctx, bricks, cam, p)
+                assert np.array_equal(got_b[0], got[0]) and np.array_equal(got_b[1], got[1])
+                ref = oracle.render_image(oc, cam, oparams(p), want_cells=True)
+                assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
+                assert np.max(np.abs(got[0].astype(np.float64) - ref[0])) <= (1e-4 if bil else 1e-5)
+        finally:
+            fnr.fnr_cache_free(ctx, dense)
+            fnr.fnr_cache_free(ctx, bricks)
