@@ -158,7 +158,8 @@ typedef struct {
     int32_t n_layers;  /* 1..16 */
     int32_t pe_in;     /* raw inputs: 3 (position) */
     int32_t pe_freqs;  /* L */
-    int32_t dims[17];  /* dims[0] = padded encoded width, dims[n_layers] = outputs */
+    int32_t dims[17];  /* dims[0] = padded encoded width (6 pe_freqs .. 64), other widths 1..256,
+                          dims[n_layers] = outputs; wider inputs: FNR_ERR_UNSUPPORTED */
     const uint16_t *weights[16];
     const float *biases[16];
 } fnr_mlp;

@@ -3,26 +3,31 @@
 // Section 3.2 Eqs. 3-4 and Section 4: F_pos and F_dir are ReLU MLPs on
 // positionally encoded inputs).
 //
-// One CTA per SM walks tiles of 128 grid points with three warp roles:
+// One CTA per SM walks tiles of 128 grid points with four warp roles:
 //   producer (warp 0): streams every layer's bf16 weights, pre-arranged in
 //     64-column K chunks of the K-major 128-byte swizzled operand layout,
-//     through a 3-slot shared-memory ring by bulk async copy (cp.async.bulk,
+//     through a 2-slot shared-memory ring by bulk async copy (cp.async.bulk,
 //     completion on the slot's "full" mbarrier), running ahead across layers
 //     and tiles;
 //   two tiles are in flight: each has its own A tile (same swizzled layout)
 //     and its own tensor-memory accumulator, so one tile's epilogue runs while
 //     the other's MMAs do;
+//   encoders (warps 2-3): encode each tile's points (gamma(x) = sin / cos(2^j
+//     pi x), rounded to bf16) into the tile's layer-0 staging buffer one tile
+//     pair ahead, as soon as the MMAs that read the buffer's previous contents
+//     have completed, so encoding never waits between tiles;
 //   MMA issuer (warp 1, one lane): waits for the layer input and each chunk,
 //     issues tcgen05.mma (M=128, N=layer width, K=16 steps, bf16 x bf16 ->
-//     fp32 in tensor memory), releases each slot with tcgen05.commit on its
-//     "empty" mbarrier and signals the finished accumulator with one more commit;
-//   epilogue (warps 4-19, four per 32-lane quarter of tensor memory): encode
-//     the tile's points (gamma(x) = sin / cos(2^j pi x), rounded to bf16) into
-//     the A tile, then per layer read the accumulator (tcgen05.ld), add the
-//     bias, apply ReLU, round to bf16 and write the next layer's A tile -- or,
-//     after the head, write sigma = ReLU(out_0), (u, v, w) = out_1..3D (F_pos)
-//     or beta = out_0..D-1 (F_dir) straight into the cache, then encode the
-//     tile's next points while the other tile is still in flight.
+//     fp32 in tensor memory; layer 0 reads the staging buffer), releases each
+//     slot with tcgen05.commit on its "empty" mbarrier and signals the
+//     finished accumulator with one more commit;
+//   epilogue (warps 4-19, four per 32-lane quarter of tensor memory): per
+//     hidden layer read the accumulator (tcgen05.ld), add the bias, apply
+//     ReLU, round to bf16 and write the next layer's A tile; after the head,
+//     stage the outputs in the (now free) A tile as fp32 rows and write the
+//     tile's sigma = ReLU(out_0), (u, v, w) = out_1..3D (F_pos) or beta =
+//     out_0..D-1 (F_dir) -- contiguous ranges of the cache -- with coalesced
+//     stores by all sixteen warps.
 // The next layer's weights load while the epilogue runs. Every mbarrier wait
 // is bounded; a wait that runs out sets the error word and a CTA-wide abort
 // flag, every role leaves its loop, and the tensor memory is freed.
@@ -54,7 +59,7 @@ constexpr int kChunkK = 64;                          // K columns per weight chu
 #define FNR_MLP_CLUSTER 1
 #endif
 #ifndef FNR_MLP_SLOTS
-#define FNR_MLP_SLOTS 3
+#define FNR_MLP_SLOTS 2
 #endif
 #ifndef FNR_MLP_PAIR
 #define FNR_MLP_PAIR 2
@@ -69,23 +74,28 @@ constexpr int kPair = FNR_MLP_PAIR;                  // tiles in flight per CTA
 #ifndef FNR_MLP_FIRST_EPI
 #define FNR_MLP_FIRST_EPI 4
 #endif
-#ifndef FNR_MLP_LD4
-#define FNR_MLP_LD4 0
-#endif
 #ifndef FNR_MLP_KATTR
 #define FNR_MLP_KATTR __launch_bounds__(kThreads, 1)
 #endif
 // epilogue warp w reads tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31
-constexpr int kProducerWarp = 0, kMmaWarp = 1, kFirstEpiWarp = FNR_MLP_FIRST_EPI, kEpiWarps = 16;
+constexpr int kProducerWarp = 0, kMmaWarp = 1, kEncWarp0 = 2, kEncWarps = 2;
+constexpr int kFirstEpiWarp = FNR_MLP_FIRST_EPI, kEpiWarps = 16;
+static_assert(kFirstEpiWarp >= kEncWarp0 + kEncWarps && kFirstEpiWarp % 4 == 0, "warp roles");
 constexpr int kThreads = (kFirstEpiWarp + kEpiWarps) * 32;
+constexpr int kMaxK0 = kChunkK;     // the encoded input (layer 0's K) fits one staging chunk
+constexpr int kMaxHeadOut = 64;     // outputs per point staged after the head
 constexpr int kMaxLayers = 16;
 constexpr int kMaxBias = kMaxLayers * kMaxN;
 constexpr uint32_t kTmemCols = 256 * kPair;                                // one accumulator per tile
 constexpr size_t kSmemA = size_t(kPair) * kTileM * kMaxK * 2;               // 64 KB activations per tile
+constexpr size_t kStageBytes = size_t(kTileM) * kMaxK0 * 2;                 // 16 KB layer-0 input per tile
+constexpr size_t kSmemStage = size_t(kPair) * kStageBytes;
 constexpr size_t kSmemRing = size_t(kSlots) * kSlotBytes;                   // weight chunks
 constexpr size_t kSmemBias = FNR_MLP_BIAS_SMEM ? size_t(kMaxBias) * 4 : 0;  // 16 KB biases (else read via L1)
-constexpr size_t kSmemBars = (size_t(2 * kSlots + 2 * kPair) * 8 + 16 + 127) / 128 * 128;
-constexpr size_t kSmemBytes = kSmemA + kSmemRing + kSmemBias + kSmemBars + 1024;  // + alignment slack
+constexpr int kBars = 2 * kSlots + 5 * kPair;  // full, empty; acc_full, a_ready, enc_ready, enc_free, head_ready
+constexpr size_t kSmemBars = (size_t(kBars) * 8 + 16 + 127) / 128 * 128;
+constexpr size_t kSmemBytes = kSmemA + kSmemStage + kSmemRing + kSmemBias + kSmemBars + 1024;  // + alignment slack
+static_assert(size_t(kTileM) * (kMaxHeadOut + 4) * 4 <= size_t(kTileM) * kMaxK * 2, "head staging fits an A tile");
 static_assert(kSmemBytes <= 232448, "shared memory per CTA");
 constexpr long long kWaitLimit = 1LL << 22;                                 // try_wait polls before giving up
 
@@ -116,6 +126,8 @@ struct MlpArgs {
     const float *points;  // [n_points][3]
     float *out;
     int out_stride, relu0;
+    int n_out;        // outputs stored per point: 1 + 3D (mode 0), D (mode 1), out_stride (mode 2)
+    int head_stride;  // floats per staged head row: round16(n_out) + 4
     int *err;
 };
 
@@ -308,19 +320,30 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
     extern __shared__ __align__(1024) char smem_raw[];
     // the swizzled operand tiles start on 1024-byte boundaries
     char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    char *sa = smem;  // A tile of slot t at sa + t * kTileM * kMaxK * 2
-    char *ring = smem + kSmemA;
-    float *sbias = reinterpret_cast<float *>(smem + kSmemA + kSmemRing);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kSmemA + kSmemRing + kSmemBias);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kSlots + 2 * kPair);
+    char *sa = smem;                 // A tile of slot t at sa + t * kTileM * kMaxK * 2
+    char *stage = smem + kSmemA;     // layer-0 input of slot t at stage + t * kStageBytes
+    char *ring = stage + kSmemStage;
+    float *sbias = reinterpret_cast<float *>(ring + kSmemRing);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ring + kSmemRing + kSmemBias);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kBars);
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // bars: [0, kSlots) full, [kSlots, 2 kSlots) empty, then acc_full[kPair], then a_ready[kPair]
+    // bars: [0, kSlots) full, [kSlots, 2 kSlots) empty, then per tile slot: acc_full, a_ready, enc_ready,
+    // enc_free, head_ready
     const uint32_t bar0 = smem_u32(bars);
     auto full_bar = [&](int s) { return bar0 + 8u * uint32_t(s); };
     auto empty_bar = [&](int s) { return bar0 + 8u * uint32_t(kSlots + s); };
-    auto acc_full = [&](int t) { return bar0 + 8u * uint32_t(2 * kSlots + t); };
-    auto a_ready = [&](int t) { return bar0 + 8u * uint32_t(2 * kSlots + kPair + t); };
+    auto tile_bar = [&](int which, int t) { return bar0 + 8u * uint32_t(2 * kSlots + which * kPair + t); };
+    // acc_full(t): the tile's accumulator holds a finished layer (one tcgen05.commit)
+    auto acc_full = [&](int t) { return tile_bar(0, t); };
+    // a_ready(t): the accumulator has been read and the next layer's A tile written (every epilogue warp)
+    auto a_ready = [&](int t) { return tile_bar(1, t); };
+    // enc_ready(t): the staging buffer holds the encoded points of the tile's next pair (both encoder warps)
+    auto enc_ready = [&](int t) { return tile_bar(2, t); };
+    // enc_free(t): the layer-0 MMAs that read the staging buffer have completed (one tcgen05.commit)
+    auto enc_free = [&](int t) { return tile_bar(3, t); };
+    // head_ready(t): every epilogue warp has staged its head outputs
+    auto head_ready = [&](int t) { return tile_bar(4, t); };
     constexpr uint32_t kATileBytes = uint32_t(kTileM) * kMaxK * 2;
 
     if (FNR_MLP_BIAS_SMEM)
@@ -333,6 +356,9 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
         for (int t = 0; t < kPair; ++t) {
             mbar_init(acc_full(t), 1);
             mbar_init(a_ready(t), kEpiWarps);
+            mbar_init(enc_ready(t), kEncWarps);
+            mbar_init(enc_free(t), 1);
+            mbar_init(head_ready(t), kEpiWarps);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -360,6 +386,12 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
     // CTA has the most tiles, the others carry empty ones
     const long long bid0 = (long long)blockIdx.x - crank;
     const long long n_pairs = n_tiles > bid0 ? (n_tiles - bid0 + kPair * G - 1) / (kPair * G) : 0;
+    // a warp-wide bounded wait (lane 0 polls); false when it ran out or another role aborted
+    auto warp_wait = [&](uint32_t bar, uint32_t parity) {
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait(bar, parity, A.err, &abort_flag) ? 1 : 0;
+        return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    };
 
     if (warp == kProducerWarp) {
         if (lane == 0) {
@@ -400,10 +432,13 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                 for (int li = 0; li < A.n_layers && !abort_flag; ++li, ++uses)
                     for (int t = 0; t < kPair && !abort_flag; ++t) {
                         const MlpLayerDev &Ly = A.L[li];
+                        if (li == 0 && !mbar_wait(enc_ready(t), uint32_t(r & 1), A.err, &abort_flag)) break;
                         if (!mbar_wait(a_ready(t), uint32_t(uses & 1), A.err, &abort_flag)) break;
                         tc_fence_after();
                         const uint32_t idesc = instr_desc(kTileM, Ly.N);
-                        const uint32_t a_base = smem_u32(sa) + uint32_t(t) * kATileBytes;
+                        const uint32_t a_base =
+                            li == 0 ? smem_u32(stage) + uint32_t(t) * uint32_t(kStageBytes)
+                                    : smem_u32(sa) + uint32_t(t) * kATileBytes;
                         const uint32_t d_tmem = tmem + uint32_t(t * 256);
                         const int nc = n_chunks(Ly.K);
                         for (int c = 0; c < nc; ++c, ++it) {
@@ -422,26 +457,42 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                             else umma_commit_multicast(empty_bar(slot), kCtaMask);
                         }
                         if (abort_flag) break;
+                        if (li == 0) umma_commit(enc_free(t));  // the staging buffer may be refilled
                         umma_commit(acc_full(t));
                     }
+        }
+    } else if (warp >= kEncWarp0 && warp < kEncWarp0 + kEncWarps) {
+        // encoders: rows (warp - kEncWarp0) * 32 + lane + 32 kEncWarps i of each tile
+        const int e = warp - kEncWarp0;
+        for (long long r = 0; r < n_pairs && !abort_flag; ++r) {
+            bool ok = true;
+            for (int t = 0; t < kPair && ok; ++t) {
+                // pair r - 1's layer-0 MMAs of this slot have read the buffer
+                if (r > 0 && !(ok = warp_wait(enc_free(t), uint32_t((r - 1) & 1)))) break;
+                const long long tile = pair_tile(r, t);
+                char *st = stage + size_t(t) * kStageBytes;
+                for (int row = e * 32 + lane; row < kTileM; row += 32 * kEncWarps) {
+                    const long long p = tile < n_tiles ? tile * kTileM + row : A.n_points;  // past the end: zeros
+                    encode_point(A, p, row, st, 0, 1);
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(enc_ready(t));
+            }
+            if (!ok) break;
         }
     } else if (warp >= kFirstEpiWarp) {
         const int q = warp & 3, g = (warp - kFirstEpiWarp) >> 2;  // lane quarter, column group
         const int row = q * 32 + lane;
+        const int te = (warp - kFirstEpiWarp) * 32 + lane;       // 0 .. 32 kEpiWarps - 1
         long long uses = 0;
         bool stop = false;
-        long long pt[kPair];
-        // encode tile t of group r into A tile t (its previous tile's head has been read) and release it
-        auto encode_tile = [&](long long r, int t) {
-            const long long tile = pair_tile(r, t);
-            pt[t] = tile < n_tiles ? tile * kTileM + row : A.n_points;  // past the end: invalid row
-            encode_point(A, pt[t], row, sa + size_t(t) * kATileBytes, g, 4);
-            fence_proxy_async();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(a_ready(t));
-        };
+        // the accumulators are free for the first pair's layer 0
         if (n_pairs > 0)
-            for (int t = 0; t < kPair; ++t) encode_tile(0, t);
+            for (int t = 0; t < kPair; ++t) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(a_ready(t));
+            }
         for (long long r = 0; r < n_pairs && !stop; ++r) {
             for (int li = 0; li < A.n_layers && !stop; ++li, ++uses) {
                 const MlpLayerDev &Ly = A.L[li];
@@ -449,107 +500,124 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                 const bool last = li + 1 == A.n_layers;
                 const float *bias = (FNR_MLP_BIAS_SMEM ? sbias : A.bias) + Ly.bias_off;
                 for (int t = 0; t < kPair; ++t) {
-                    int ok = 1;
-                    if (lane == 0) ok = mbar_wait(acc_full(t), uint32_t(uses & 1), A.err, &abort_flag) ? 1 : 0;
-                    ok = __shfl_sync(0xffffffffu, ok, 0);
-                    if (!ok) {
+                    if (!warp_wait(acc_full(t), uint32_t(uses & 1))) {
                         stop = true;
                         break;
                     }
                     tc_fence_after();
-                    const long long p = pt[t];
-                    const bool valid = p < A.n_points;
                     char *sa_t = sa + size_t(t) * kATileBytes;
                     const uint32_t trow = tmem + uint32_t(t * 256) + (uint32_t(q * 32) << 16);
-                    // this warp's 16-column chunks j = g, g+4, g+8, g+12, two loads in flight per wait
-                    const int nj = N / 16;
-                    auto process = [&](const uint32_t (&rr)[16], int j) {
-                        const int c0 = j * 16;
-                        float v[16];
-#pragma unroll
-                        for (int u = 0; u < 16; u += 4) {
-                            const float4 b4 = FNR_MLP_BIAS_SMEM ? *reinterpret_cast<const float4 *>(bias + c0 + u)
-                                                                : __ldg(reinterpret_cast<const float4 *>(bias + c0 + u));
-                            v[u + 0] = __uint_as_float(rr[u + 0]) + b4.x;
-                            v[u + 1] = __uint_as_float(rr[u + 1]) + b4.y;
-                            v[u + 2] = __uint_as_float(rr[u + 2]) + b4.z;
-                            v[u + 3] = __uint_as_float(rr[u + 3]) + b4.w;
-                        }
-                        if (!last) {
+                    if (!last) {
+                        // this warp's 16-column chunks j = g, g+4, g+8, g+12, two loads in flight per wait
+                        const int nj = N / 16;
+                        auto process = [&](const uint32_t (&rr)[16], int j) {
+                            const int c0 = j * 16;
 #pragma unroll
                             for (int u = 0; u < 16; u += 8) {
+                                const float4 b0 = FNR_MLP_BIAS_SMEM
+                                                      ? *reinterpret_cast<const float4 *>(bias + c0 + u)
+                                                      : __ldg(reinterpret_cast<const float4 *>(bias + c0 + u));
+                                const float4 b1 = FNR_MLP_BIAS_SMEM
+                                                      ? *reinterpret_cast<const float4 *>(bias + c0 + u + 4)
+                                                      : __ldg(reinterpret_cast<const float4 *>(bias + c0 + u + 4));
                                 uint4 pk;
-                                pk.x = pack_bf16(fmaxf(v[u + 0], 0.0f), fmaxf(v[u + 1], 0.0f));
-                                pk.y = pack_bf16(fmaxf(v[u + 2], 0.0f), fmaxf(v[u + 3], 0.0f));
-                                pk.z = pack_bf16(fmaxf(v[u + 4], 0.0f), fmaxf(v[u + 5], 0.0f));
-                                pk.w = pack_bf16(fmaxf(v[u + 6], 0.0f), fmaxf(v[u + 7], 0.0f));
+                                pk.x = pack_bf16(fmaxf(__uint_as_float(rr[u + 0]) + b0.x, 0.0f),
+                                                 fmaxf(__uint_as_float(rr[u + 1]) + b0.y, 0.0f));
+                                pk.y = pack_bf16(fmaxf(__uint_as_float(rr[u + 2]) + b0.z, 0.0f),
+                                                 fmaxf(__uint_as_float(rr[u + 3]) + b0.w, 0.0f));
+                                pk.z = pack_bf16(fmaxf(__uint_as_float(rr[u + 4]) + b1.x, 0.0f),
+                                                 fmaxf(__uint_as_float(rr[u + 5]) + b1.y, 0.0f));
+                                pk.w = pack_bf16(fmaxf(__uint_as_float(rr[u + 6]) + b1.z, 0.0f),
+                                                 fmaxf(__uint_as_float(rr[u + 7]) + b1.w, 0.0f));
                                 *reinterpret_cast<uint4 *>(sa_t + a_offset(row, c0 + u)) = pk;
                             }
-                        } else if (valid) {
-#pragma unroll
-                            for (int u = 0; u < 16; ++u) {
-                                const int c = c0 + u;
-                                const float o = v[u];
-                                if (A.mode == 2) {
-                                    if (c < A.out_stride)
-                                        A.out[p * A.out_stride + c] = (c == 0 && A.relu0) ? fmaxf(o, 0.0f) : o;
-                                } else if (A.mode == 0) {
-                                    if (c == 0) {
-                                        const float sg = fmaxf(o, 0.0f);
-                                        if (A.prec == FNR_PREC_FP16)
-                                            static_cast<__half *>(A.sigma_out)[p] = __float2half_rn(sg);
-                                        else static_cast<float *>(A.sigma_out)[p] = sg;
-                                    } else if (c <= 3 * A.D) {
-                                        char *rec = A.uvw_out + p * A.rec_stride;
-                                        if (A.prec == FNR_PREC_FP16)
-                                            reinterpret_cast<__half *>(rec)[c - 1] = __float2half_rn(o);
-                                        else reinterpret_cast<float *>(rec)[c - 1] = o;
-                                    }
-                                } else if (c < A.D) {
-                                    if (A.dprec == FNR_PREC_FP16)
-                                        static_cast<__half *>(A.beta_out)[p * A.D + c] = __float2half_rn(o);
-                                    else static_cast<float *>(A.beta_out)[p * A.D + c] = o;
-                                }
-                            }
+                        };
+                        for (int j0 = g; j0 < nj; j0 += 8) {  // warp-uniform
+                            uint32_t r0[16], r1[16];
+                            const bool two = j0 + 4 < nj;
+                            tmem_ld16_nowait(trow + uint32_t(j0 * 16), r0);
+                            if (two) tmem_ld16_nowait(trow + uint32_t((j0 + 4) * 16), r1);
+                            tmem_wait();
+                            process(r0, j0);
+                            if (two) process(r1, j0 + 4);
                         }
-                    };
-#if FNR_MLP_LD4
-                    for (int j0 = g; j0 < nj; j0 += 16) {  // warp-uniform: up to four loads per wait
-                        uint32_t rr[4][16];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            if (j0 + 4 * i < nj) tmem_ld16_nowait(trow + uint32_t((j0 + 4 * i) * 16), rr[i]);
-                        tmem_wait();
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            if (j0 + 4 * i < nj) process(rr[i], j0 + 4 * i);
-                    }
-#else
-                    for (int j0 = g; j0 < nj; j0 += 8) {  // warp-uniform
-                        uint32_t r0[16], r1[16];
-                        const bool two = j0 + 4 < nj;
-                        tmem_ld16_nowait(trow + uint32_t(j0 * 16), r0);
-                        if (two) tmem_ld16_nowait(trow + uint32_t((j0 + 4) * 16), r1);
-                        tmem_wait();
-                        process(r0, j0);
-                        if (two) process(r1, j0 + 4);
-                    }
-#endif
-                    if (!last) {  // K padding of the next layer: columns [N, roundup(N, 64)) are 0
+                        // K padding of the next layer: columns [N, roundup(N, 64)) are 0
                         const uint4 z = make_uint4(0u, 0u, 0u, 0u);
                         for (int c8 = N + 8 * g; c8 < ((N + 63) & ~63); c8 += 32)
                             *reinterpret_cast<uint4 *>(sa_t + a_offset(row, c8)) = z;
-                    }
-                    tc_fence_before();
-                    if (!last) {
+                        tc_fence_before();
                         fence_proxy_async();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(a_ready(t));
-                    } else {
-                        __syncwarp();
-                        // the next group's tile t, encoded while the other tile is still in flight
-                        if (r + 1 < n_pairs) encode_tile(r + 1, t);
+                        continue;
                     }
+                    // head: stage out_c + bias (c < n_out) as fp32 rows of head_stride floats in the A tile,
+                    // which the head's MMAs no longer read
+                    float *hst = reinterpret_cast<float *>(sa_t);
+                    const int hs = A.head_stride;
+                    for (int j = g; j * 16 < A.n_out; j += 4) {  // warp-uniform
+                        uint32_t rr[16];
+                        tmem_ld16_nowait(trow + uint32_t(j * 16), rr);
+                        tmem_wait();
+#pragma unroll
+                        for (int u = 0; u < 16; u += 4) {
+                            const float4 b4 = FNR_MLP_BIAS_SMEM
+                                                  ? *reinterpret_cast<const float4 *>(bias + j * 16 + u)
+                                                  : __ldg(reinterpret_cast<const float4 *>(bias + j * 16 + u));
+                            *reinterpret_cast<float4 *>(hst + row * hs + j * 16 + u) =
+                                make_float4(__uint_as_float(rr[u + 0]) + b4.x, __uint_as_float(rr[u + 1]) + b4.y,
+                                            __uint_as_float(rr[u + 2]) + b4.z, __uint_as_float(rr[u + 3]) + b4.w);
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(head_ready(t));
+                    if (!warp_wait(head_ready(t), uint32_t(r & 1))) {
+                        stop = true;
+                        break;
+                    }
+                    // the tile's outputs are contiguous ranges of the cache (or of out): element e of the
+                    // range belongs to row e / n and output e % n
+                    const long long tile = pair_tile(r, t);
+                    const long long p0 = tile * kTileM;
+                    const int nv = tile < n_tiles ? int(A.n_points - p0 < kTileM ? A.n_points - p0 : kTileM) : 0;
+                    constexpr int kEpiThreads = 32 * kEpiWarps;
+                    if (A.mode == 0) {
+                        for (int i = te; i < nv; i += kEpiThreads) {
+                            const float sg = fmaxf(hst[i * hs], 0.0f);
+                            if (A.prec == FNR_PREC_FP16) static_cast<__half *>(A.sigma_out)[p0 + i] = __float2half_rn(sg);
+                            else static_cast<float *>(A.sigma_out)[p0 + i] = sg;
+                        }
+                        const int n = 3 * A.D;
+                        char *rec0 = A.uvw_out + p0 * A.rec_stride;
+                        for (int e = te; e < nv * n; e += kEpiThreads) {
+                            const int i = e / n, c = e - i * n;
+                            const float o = hst[i * hs + 1 + c];
+                            char *rec = rec0 + size_t(i) * A.rec_stride;
+                            if (A.prec == FNR_PREC_FP16) reinterpret_cast<__half *>(rec)[c] = __float2half_rn(o);
+                            else reinterpret_cast<float *>(rec)[c] = o;
+                        }
+                    } else if (A.mode == 1) {
+                        const int n = A.D;
+                        for (int e = te; e < nv * n; e += kEpiThreads) {
+                            const int i = e / n, c = e - i * n;
+                            const float o = hst[i * hs + c];
+                            if (A.dprec == FNR_PREC_FP16)
+                                static_cast<__half *>(A.beta_out)[p0 * n + e] = __float2half_rn(o);
+                            else static_cast<float *>(A.beta_out)[p0 * n + e] = o;
+                        }
+                    } else {
+                        const int n = A.out_stride;
+                        for (int e = te; e < nv * n; e += kEpiThreads) {
+                            const int i = e / n, c = e - i * n;
+                            const float o = hst[i * hs + c];
+                            A.out[p0 * n + e] = (c == 0 && A.relu0) ? fmaxf(o, 0.0f) : o;
+                        }
+                    }
+                    // the staged rows have been read: the next pair's layer 0 may use the accumulator
+                    // and its epilogue may overwrite the A tile
+                    __syncwarp();
+                    if (r + 1 < n_pairs && lane == 0) mbar_arrive(a_ready(t));
                 }
             }
         }
@@ -597,6 +665,8 @@ fnr_status check_mlp(const fnr_mlp *m, int n_out_min, const char *name) {
     if (m->pe_freqs < 1 || 6 * m->pe_freqs > m->dims[0])
         return fail(FNR_ERR_INVALID_ARG, "%s: dims[0]=%d cannot hold 2*3*%d encoded inputs", name, m->dims[0],
                     m->pe_freqs);
+    if (m->dims[0] > kMaxK0)
+        return fail(FNR_ERR_UNSUPPORTED, "%s: encoded width dims[0]=%d above %d", name, m->dims[0], kMaxK0);
     for (int i = 0; i <= m->n_layers; ++i)
         if (m->dims[i] < 1 || round64(m->dims[i]) > kMaxK)
             return fail(FNR_ERR_UNSUPPORTED, "%s: layer width %d outside [1, %d]", name, m->dims[i], kMaxK);
@@ -648,6 +718,10 @@ fnr_status mlp_launch(const fnr_mlp *m, MlpArgs &A, int num_sms, cudaStream_t s)
     A.n_layers = m->n_layers;
     A.pe_freqs = m->pe_freqs;
     A.err = static_cast<int *>(ebuf.p);
+    A.n_out = A.mode == 0 ? 1 + 3 * A.D : (A.mode == 1 ? A.D : A.out_stride);
+    A.head_stride = round16(A.n_out) + 4;
+    if (A.n_out < 1 || A.n_out > kMaxHeadOut || A.n_out > A.L[m->n_layers - 1].N)
+        return fail(FNR_ERR_UNSUPPORTED, "MLP kernel: %d outputs per point (at most %d)", A.n_out, kMaxHeadOut);
     if (A.n_points <= 0) return FNR_OK;
     if ((e = cudaFuncSetAttribute(mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes))) !=
         cudaSuccess)

@@ -195,3 +195,16 @@ def test_widths_not_multiple_of_64(fnr):
         check_channels(beta, oracle.mlp_eval(as_fp64(dirn), dirs, 4, True))
     finally:
         fnr.fnr_context_destroy(ctx)
+
+
+def test_encoded_width_above_64_rejected(fnr):
+    """The encoded input must fit one 64-column staging chunk: dims[0] = 128 is refused before any launch."""
+    pos = scenegen.mlp_weights(5, [128, 32, 25], bias_scale=0.3)
+    dirn = scenegen.mlp_weights(6, [24, 16, 8], bias_scale=0.3)
+    ctx = fnr.fnr_context_create(0, 0)
+    try:
+        with pytest.raises(fnr.FnrError) as ei:
+            build(fnr, ctx, 8, 8, 8, pos, dirn)
+        assert ei.value.status == fnr.FNR_ERR_UNSUPPORTED
+    finally:
+        fnr.fnr_context_destroy(ctx)
