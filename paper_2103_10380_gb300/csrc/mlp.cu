@@ -263,44 +263,62 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return uint32_t(__bfloat16_as_ushort(x)) | (uint32_t(__bfloat16_as_ushort(y)) << 16);
 }
 
-// Positional encoding of point p into row `row` of the A tile: the 8-column
-// groups g0, g0 + gstep, ... (the four epilogue warps of a row share them).
-__device__ __forceinline__ void encode_point(const MlpArgs &A, long long p, int row, char *sa, int g0, int gstep) {
+// Positional encoding of point p into row `row` of a layer-0 A tile (K0 <= 64
+// columns, one 128-byte swizzled row): column 2 P + 0 / 1 holds sin / cos(2^j
+// pi x_a) with P = a L + j, rounded to bf16; columns from 6 L on, and every
+// column of a point past the end, are 0.
+__device__ __forceinline__ void encode_point(const MlpArgs &A, long long p, int row, char *sa) {
     const int K0 = A.L[0].K;
-    float x[3] = {0.0f, 0.0f, 0.0f};
+    float x0 = 0.0f, x1 = 0.0f, x2 = 0.0f;
     const bool valid = p < A.n_points;
     if (valid) {
         if (A.mode == 2) {
-            x[0] = A.points[3 * p];
-            x[1] = A.points[3 * p + 1];
-            x[2] = A.points[3 * p + 2];
+            x0 = A.points[3 * p];
+            x1 = A.points[3 * p + 1];
+            x2 = A.points[3 * p + 2];
         } else if (A.mode == 0) {
-            const long long kk = A.k;
-            const int ix = int(p % kk), iy = int((p / kk) % kk), iz = int(p / (kk * kk));
-            x[0] = fmaf(float(ix) + 0.5f, A.h[0], A.bmin[0]);
-            x[1] = fmaf(float(iy) + 0.5f, A.h[1], A.bmin[1]);
-            x[2] = fmaf(float(iz) + 0.5f, A.h[2], A.bmin[2]);
+            int ix, iy, iz;
+            if (A.n_points <= 0x7fffffffLL) {  // 32-bit index arithmetic
+                const unsigned k = unsigned(A.k), q = unsigned(p);
+                const unsigned yz = q / k;
+                ix = int(q - yz * k);
+                iz = int(yz / k);
+                iy = int(yz - unsigned(iz) * k);
+            } else {
+                const long long kk = A.k;
+                ix = int(p % kk);
+                iy = int((p / kk) % kk);
+                iz = int(p / (kk * kk));
+            }
+            x0 = fmaf(float(ix) + 0.5f, A.h[0], A.bmin[0]);
+            x1 = fmaf(float(iy) + 0.5f, A.h[1], A.bmin[1]);
+            x2 = fmaf(float(iz) + 0.5f, A.h[2], A.bmin[2]);
         } else {
-            const int it = int(p / A.l), ip = int(p % A.l);
+            const unsigned q = unsigned(p), l = unsigned(A.l);
+            const int it = int(q / l), ip = int(q - unsigned(it) * l);
             float st, ct, sp, cp;
             sincospif((float(it) + 0.5f) / float(A.l), &st, &ct);         // theta / pi
             sincospif(2.0f * (float(ip) + 0.5f) / float(A.l), &sp, &cp);  // phi / pi
-            x[0] = st * cp;
-            x[1] = st * sp;
-            x[2] = ct;
+            x0 = st * cp;
+            x1 = st * sp;
+            x2 = ct;
         }
     }
-    const int Lf = A.pe_freqs;
-    for (int g = g0 * 8; g < K0; g += gstep * 8) {  // 8 encoded values per 16-byte store
+    const int nP = valid ? 3 * A.pe_freqs : 0;
+    int a = 0, j = 0;  // (a, j) of P, advanced with P
+    for (int g = 0; g < K0; g += 8) {  // 8 encoded values per 16-byte store
         float v[8];
-        // column 2 P + 0 / 1 holds sin / cos(2^j pi x_a) with P = a L + j
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int P = (g >> 1) + q;
             float sv = 0.0f, cv = 0.0f;
-            if (valid && P < 3 * Lf) {
-                const int a = P / Lf, j = P - a * Lf;
-                sincospif(ldexpf(x[a], j), &sv, &cv);  // 2^j x exact
+            if (P < nP) {
+                const float xa = a == 0 ? x0 : (a == 1 ? x1 : x2);
+                sincospif(xa * __int_as_float((127 + j) << 23), &sv, &cv);  // 2^j x_a, exact
+                if (++j == A.pe_freqs) {
+                    j = 0;
+                    ++a;
+                }
             }
             v[2 * q] = sv;
             v[2 * q + 1] = cv;
@@ -473,7 +491,7 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                 char *st = stage + size_t(t) * kStageBytes;
                 for (int row = e * 32 + lane; row < kTileM; row += 32 * kEncWarps) {
                     const long long p = tile < n_tiles ? tile * kTileM + row : A.n_points;  // past the end: zeros
-                    encode_point(A, p, row, st, 0, 1);
+                    encode_point(A, p, row, st);
                 }
                 fence_proxy_async();
                 __syncwarp();
