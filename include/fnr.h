@@ -357,6 +357,11 @@ typedef struct {
     int64_t max_batch_rays;     /* rays per launch (0: 16 Mi) */
     int32_t n_slots;            /* launches in flight at once, <= 8 (0: 3) */
     int32_t use_graphs;         /* 1: each slot replays a captured CUDA graph */
+    int32_t idle_spin_us;       /* the scheduler thread keeps polling for submits and completions this
+                                   long after its last event, then sleeps until a submit (0: 5000;
+                                   -1: it never sleeps while the loop runs, for the lowest latency at
+                                   the cost of one busy host thread); < -1: INVALID_ARG */
+    int32_t reserved;           /* 0 */
 } fnr_serve_config;
 
 /* Start the request loop (a host scheduler thread plus n_slots streams).

@@ -108,7 +108,8 @@ class fnr_result(ctypes.Structure):
 
 class fnr_serve_config(ctypes.Structure):
     _fields_ = [("queue_capacity", ctypes.c_int32), ("max_batch_requests", ctypes.c_int32),
-                ("max_batch_rays", ctypes.c_int64), ("n_slots", ctypes.c_int32), ("use_graphs", ctypes.c_int32)]
+                ("max_batch_rays", ctypes.c_int64), ("n_slots", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+                ("idle_spin_us", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # Every symbol include/fnr.h declares, with (argtypes, restype).
@@ -326,8 +327,9 @@ def fnr_render(ctx: int, cache: int, cams, params: fnr_render_params, rgba, stat
 
 # ------------------------------------------------------------------ serving
 def fnr_serve_start(ctx: int, queue_capacity=0, max_batch_requests=0, max_batch_rays=0, n_slots=0,
-                    use_graphs=1):
-    cfg = fnr_serve_config(queue_capacity, max_batch_requests, max_batch_rays, n_slots, use_graphs)
+                    use_graphs=1, idle_spin_us=0):
+    """idle_spin_us: how long the scheduler keeps polling after its last event (0: 5 ms; -1: always)."""
+    cfg = fnr_serve_config(queue_capacity, max_batch_requests, max_batch_rays, n_slots, use_graphs, idle_spin_us, 0)
     check(lib().fnr_serve_start(ctx, ctypes.byref(cfg)))
 
 

@@ -42,7 +42,7 @@ void budget_uncharge(fnr_context *ctx, uint64_t bytes);
 
 constexpr int kMaxBatch = 64;
 constexpr int kMaxSlots = 8;
-constexpr uint64_t kSpinAfterActivityNs = 5000000;  // keep polling 5 ms after the last event
+constexpr uint64_t kSpinAfterActivityNs = 5000000;  // default: keep polling 5 ms after the last event
 
 struct ServeFrame {
     CacheView c;
@@ -207,6 +207,8 @@ struct Slot {
 struct Server {
     fnr_context *ctx = nullptr;
     fnr_serve_config cfg;
+    uint64_t spin_after_ns = kSpinAfterActivityNs;
+    bool spin_forever = false;
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
     std::deque<uint64_t> pending;
@@ -417,7 +419,7 @@ struct Server {
             // Completion words are polled, not waited on. While work is in flight,
             // and for a short while after the last activity (requests tend to come
             // in bursts), the thread spins; otherwise it sleeps until a submit.
-            if (busy || !pending.empty() || now - last_activity_ns < kSpinAfterActivityNs) {
+            if (busy || !pending.empty() || spin_forever || now - last_activity_ns < spin_after_ns) {
                 lk.unlock();
                 std::this_thread::yield();
                 lk.lock();
@@ -439,11 +441,15 @@ static fnr_status server_start(fnr_context *ctx, const fnr_serve_config *cfg_in)
     if (cfg.max_batch_rays <= 0) cfg.max_batch_rays = int64_t(16) << 20;
     if (cfg.n_slots <= 0) cfg.n_slots = 3;
     if (cfg.n_slots > kMaxSlots) return fail(FNR_ERR_INVALID_ARG, "n_slots > %d", kMaxSlots);
+    if (cfg.idle_spin_us < -1) return fail(FNR_ERR_INVALID_ARG, "idle_spin_us %d < -1", cfg.idle_spin_us);
+    if (cfg.reserved != 0) return fail(FNR_ERR_INVALID_ARG, "reserved field of fnr_serve_config is not 0");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     Server *sv = new Server();
     sv->ctx = ctx;
     sv->cfg = cfg;
+    sv->spin_forever = cfg.idle_spin_us == -1;
+    if (cfg.idle_spin_us > 0) sv->spin_after_ns = uint64_t(cfg.idle_spin_us) * 1000u;
     sv->slots.resize(cfg.n_slots);
     fnr_status st = FNR_OK;
     for (Slot &s : sv->slots) {

@@ -5,6 +5,7 @@ and in a mix of requests batched into persistent launches: bit-identical,
 since both paths run the same per-tile march. One served result is also checked
 against the FP64 oracle (counters bit-exact, RGBA within 1e-5)."""
 
+import ctypes
 import threading
 
 import numpy as np
@@ -218,5 +219,35 @@ def test_concurrent_submitters(fnr, scenes):
             for c, o in zip(cams, outs):
                 ref, _ = alone(fnr, ctx, cache, c, p)
                 assert np.array_equal(ref, o.cpu().numpy())
+    finally:
+        fnr.fnr_context_destroy(ctx)
+
+
+@pytest.mark.parametrize("idle_spin_us", [-1, 1, 0])
+def test_scheduler_idle_spin(fnr, scenes, idle_spin_us):
+    """The scheduler's idle policy (poll forever, poll 1 us after the last event then sleep, default)
+    changes when it notices work, never what it renders: requests spaced beyond the spin window still
+    complete and equal the plain render bit for bit. idle_spin_us < -1 and a non-zero reserved field
+    are refused."""
+    import time
+    import torch
+    ctx = fnr.fnr_context_create(0, 0)
+    try:
+        cache = build(fnr, ctx, scenes[0])
+        p = fnr.make_params(48)
+        for bad in ((-2, 0), (0, 1)):
+            cfg = fnr.fnr_serve_config(0, 0, 0, 0, 1, bad[0], bad[1])
+            st = fnr.lib().fnr_serve_start(ctx, ctypes.byref(cfg))
+            assert st == fnr.FNR_ERR_INVALID_ARG
+        fnr.fnr_serve_start(ctx, n_slots=2, idle_spin_us=idle_spin_us)
+        cams = scenegen.cameras(321, 4, 40, 30)
+        for c in cams:
+            out = torch.zeros(40 * 30 * 4, device="cuda")
+            t = fnr.fnr_submit(ctx, fnr.make_request(cache, c, p, out))
+            assert fnr.fnr_wait(ctx, t, 20000).status == fnr.FNR_OK
+            ref, _ = alone(fnr, ctx, cache, c, p)
+            assert np.array_equal(ref, out.cpu().numpy())
+            time.sleep(0.01)  # longer than a 1 us window: the scheduler goes to sleep in between
+        fnr.fnr_serve_stop(ctx)
     finally:
         fnr.fnr_context_destroy(ctx)
