@@ -44,6 +44,8 @@ def parse():
                     help="arrival window per request rate in the serving workload (its full length is 30)")
     ap.add_argument("--only-build", action="store_true",
                     help="time only the tensor-core cache build (F_pos over k^3, F_dir over 512^2)")
+    ap.add_argument("--only-serve", action="store_true",
+                    help="run only the serving workload (three resident k^3 scenes, Poisson arrivals)")
     return ap.parse_args()
 
 
@@ -836,6 +838,17 @@ def main():
         ctx = fnr.fnr_context_create(0, 0)
         print(json.dumps({"cache_build": cache_build(fnr, torch, ctx, k=args.k)}), flush=True)
         fnr.fnr_context_destroy(ctx)
+        return
+    if args.only_serve:
+        import torch
+        import scenegen
+        import paper_2103_10380_gb300 as fnr
+        torch.cuda.set_device(0)
+        w = make_workload(args.k)
+        sig, uvw = scenegen.fill_position_grid(w.scene, w.k)
+        beta = scenegen.direction_grid(w.scene, w.l)
+        out = serving_config(fnr, torch, torch.device("cuda", 0), w, sig, uvw, beta, args.serve_seconds)
+        print(json.dumps({"serving": out}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
