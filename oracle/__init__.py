@@ -43,7 +43,7 @@ class _Camera(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("t_near", ctypes.c_float), ("t_far", ctypes.c_float),
                 ("t_thr", ctypes.c_float), ("bg", ctypes.c_float * 3), ("act", ctypes.c_int32),
-                ("skip_empty", ctypes.c_int32), ("dir_bilinear", ctypes.c_int32)]
+                ("skip_empty", ctypes.c_int32), ("dir_bilinear", ctypes.c_int32), ("voxels", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -82,6 +82,8 @@ def lib():
         L.orc_bytes_fastnerf_dir.restype = ctypes.c_uint64
         L.orc_ray.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P]
         L.orc_ray.restype = None
+        L.orc_voxel_walk.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_int32, P, P]
+        L.orc_voxel_walk.restype = ctypes.c_int32
         L.orc_phi_key.argtypes = [ctypes.c_float, ctypes.c_float]; L.orc_phi_key.restype = ctypes.c_float
         L.orc_dir_cell.argtypes = [ctypes.c_int, P, P, P]; L.orc_dir_cell.restype = None
         L.orc_dt.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int32]; L.orc_dt.restype = ctypes.c_float
@@ -192,14 +194,34 @@ def camera_struct(cam: dict) -> _Camera:
 
 
 def params_struct(N, t_near=2.0, t_far=6.0, t_thr=1e-4, bg=(1.0, 1.0, 1.0), act=ACT_SIGMOID,
-                  skip_empty=False, dir_bilinear=False) -> _Params:
+                  skip_empty=False, dir_bilinear=False, voxels=False) -> _Params:
     p = _Params()
     p.N, p.t_near, p.t_far, p.t_thr = int(N), float(t_near), float(t_far), float(t_thr)
     p.bg[:] = [float(v) for v in bg]
     p.act = int(act)
     p.skip_empty = 1 if skip_empty else 0
     p.dir_bilinear = 1 if dir_bilinear else 0
+    p.voxels = 1 if voxels else 0
     return p
+
+
+def grid_scale(k, bmin=(-1.5, -1.5, -1.5), bmax=(1.5, 1.5, 1.5)) -> np.ndarray:
+    """s_a = k / (bmax_a - bmin_a) rounded to binary32, as the oracle's renderer uses it."""
+    return np.array([np.float32(float(k) / (float(b1) - float(b0))) for b0, b1 in zip(bmin, bmax)], dtype=np.float32)
+
+
+def voxel_walk(k, o, d, t_near, t_far, max_steps, bmin=(-1.5, -1.5, -1.5), bmax=(1.5, 1.5, 1.5)):
+    """The cells a ray passes through (Section 4's voxel traversal) and its length inside each:
+    (cells int32 [n], delta float32 [n]) -- the walk orc_voxel_walk defines."""
+    cells = np.zeros(max_steps, dtype=np.int32)
+    delta = np.zeros(max_steps, dtype=np.float32)
+    b = np.ascontiguousarray(bmin, dtype=np.float32)
+    sc = grid_scale(k, bmin, bmax)
+    o = np.ascontiguousarray(o, dtype=np.float32)
+    d = np.ascontiguousarray(d, dtype=np.float32)
+    n = lib().orc_voxel_walk(int(k), _p(b), _p(sc), _p(o), _p(d), float(t_near), float(t_far), int(max_steps),
+                             _p(cells), _p(delta))
+    return cells[:n].copy(), delta[:n].copy()
 
 
 # ------------------------------------------------------------------ rendering

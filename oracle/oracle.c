@@ -20,6 +20,9 @@
  *   - Supplementary "Meshing & Rendering": Beer-Lambert extinction with early
  *     ray termination; here: stop after the first sample whose transmittance
  *     falls to T_thr, decided by an exact integer optical-depth sum.
+ *   - Section 4 ("visiting every voxel"): the voxel walk, one sample per cell
+ *     the ray passes through with delta = the ray's length inside the cell
+ *     (orc_voxel_walk).
  *   - Supplementary "Cache size calculation" (second version): dense cache
  *     sizes for NeRF and FastNeRF.
  *
@@ -38,6 +41,8 @@
 #define ORC_FP32 0
 #define ORC_FP16 1
 #define ORC_FP8 2
+
+#define FNR_ORC_MAX_N 4096 /* longest voxel walk */
 
 #define ORC_ACT_SIGMOID 0
 #define ORC_ACT_IDENTITY 1
@@ -72,6 +77,7 @@ typedef struct {
     int32_t act;
     int32_t skip_empty; /* nonzero: samples in bricks without density are not looked up */
     int32_t dir_bilinear; /* nonzero: beta interpolated bilinearly in (theta, phi) between bin centres */
+    int32_t voxels;       /* nonzero: visit every cell the ray passes through (orc_voxel_walk), at most N */
 } orc_params;
 
 /* ------------------------------------------------------------ number formats */
@@ -359,6 +365,79 @@ void orc_beta_bilinear(const orc_cache *c, const float d[3], double *beta) {
                   a * (1.0 - b) * stored_beta(c, (int64_t)i1 * l + j0, i) + a * b * stored_beta(c, (int64_t)i1 * l + j1, i);
 }
 
+/* ------------------------------------------------------------ voxel walk */
+/* Section 4 integrates every voxel a ray passes through. The walk below visits
+ * the cells of the segment [t0, t1] = [max(t_near, t_enter), min(t_far, t_exit)]
+ * of the ray inside the box in order (a 3-D digital differential analyser),
+ * in binary32 with this fixed sequence, in grid units g_a(t) = t u_a + w_a:
+ *   u_a = d_a s_a, w_a = (o_a - bmin_a) s_a   (s_a = k / (bmax_a - bmin_a))
+ *   box: for u_a != 0 the axis' entry and exit times are -w_a / u_a and
+ *     (k - w_a) / u_a (the smaller one enters); u_a == 0 needs 0 <= w_a < k;
+ *     t0 = the largest entry (and t_near), t1 = the smallest exit (and t_far);
+ *     no cells unless t0 < t1
+ *   start cell c_a = floor(fma(t0, u_a, w_a)) clamped to [0, k - 1]
+ *   next crossing along a: ((c_a + 1) - w_a) / u_a for u_a > 0, (c_a - w_a) / u_a
+ *     for u_a < 0, +infinity for u_a == 0
+ *   per step: a* = the axis with the smallest crossing (x before y before z on
+ *     ties), t_next its crossing; the cell's length delta = min(t_next, t1) - t
+ *     (t = t0 at the start); the walk ends after this cell unless t_next < t1;
+ *     t = max(t, t_next); c_a* moves one cell along the ray and the walk ends
+ *     if it leaves [0, k); otherwise a*'s next crossing is recomputed.
+ * delta <= 0 (rounding at a corner) is a zero-length visit. cells[j] is the
+ * linear index (z k + y) k + x of the j-th cell, delta[j] its length; returns
+ * the number of cells, at most max_steps. */
+static float next_crossing(int32_t c, float u, float w) {
+    if (u > 0.0f) return ((float)(c + 1) - w) / u;
+    if (u < 0.0f) return ((float)c - w) / u;
+    return INFINITY;
+}
+
+int orc_voxel_walk(int32_t k, const float bmin[3], const float sc[3], const float o[3], const float d[3],
+                   float t_near, float t_far, int32_t max_steps, int32_t *cells, float *delta) {
+    const float kf = (float)k;
+    float u[3], w[3], t0 = t_near, t1 = t_far;
+    for (int a = 0; a < 3; ++a) {
+        u[a] = d[a] * sc[a];
+        w[a] = (o[a] - bmin[a]) * sc[a];
+        if (u[a] != u[a] || w[a] != w[a]) return 0;
+        if (u[a] == 0.0f) {
+            if (!(w[a] >= 0.0f && w[a] < kf)) return 0;
+        } else {
+            const float ta = -w[a] / u[a], tb = (kf - w[a]) / u[a];
+            const float lo = ta < tb ? ta : tb, hi = ta < tb ? tb : ta;
+            if (lo > t0) t0 = lo;
+            if (hi < t1) t1 = hi;
+        }
+    }
+    if (!(t0 < t1)) return 0;
+    int32_t c[3], step[3];
+    float tn[3];
+    for (int a = 0; a < 3; ++a) {
+        int32_t ci = (int32_t)floorf(fmaf(t0, u[a], w[a]));
+        c[a] = ci < 0 ? 0 : (ci > k - 1 ? k - 1 : ci);
+        step[a] = u[a] > 0.0f ? 1 : (u[a] < 0.0f ? -1 : 0);
+        tn[a] = next_crossing(c[a], u[a], w[a]);
+    }
+    float t = t0;
+    int32_t n = 0;
+    while (n < max_steps) {
+        int a = 0;
+        if (tn[1] < tn[a]) a = 1;
+        if (tn[2] < tn[a]) a = 2;
+        const float tnext = tn[a];
+        const float end = tnext < t1 ? tnext : t1;
+        cells[n] = (int32_t)(((int64_t)c[2] * k + c[1]) * k + c[0]);
+        delta[n] = end - t;
+        ++n;
+        if (!(tnext < t1)) break;
+        if (tnext > t) t = tnext;
+        c[a] += step[a];
+        if (c[a] < 0 || c[a] >= k) break;
+        tn[a] = next_crossing(c[a], u[a], w[a]);
+    }
+    return n;
+}
+
 /* ------------------------------------------------------------ one ray */
 typedef struct {
     const orc_cache *c;
@@ -390,6 +469,59 @@ static void render_ray(const ray_ctx *X, int32_t px, int32_t py, double *rgba, i
     int32_t n_steps = N, n_look = 0, n_occ = 0;
     double uvw[48];
     const float kf = (float)k;
+    if (p->voxels) {
+        /* Section 4: every cell the ray passes through is one sample whose
+         * delta is the ray's length inside it (Eq. 1 with delta_i = that length);
+         * termination sums floor(fp32(sigma delta) 2^32) against
+         * ceil(ln(1 / T_thr) 2^32). */
+        int32_t wc[FNR_ORC_MAX_N];
+        float wd[FNR_ORC_MAX_N];
+        const int32_t nw = orc_voxel_walk(k, c->bmin, X->scale, o, d, p->t_near, p->t_far, N, wc, wd);
+        n_steps = nw;
+        int terminated = 0;
+        for (int j = 0; j < nw; ++j) {
+            if (cells) cells[j] = wc[j];
+            if (!(wd[j] > 0.0f)) continue;
+            if (p->skip_empty) {
+                const int64_t B = c->occ_brick, nb = (k + B - 1) / B, cell = wc[j];
+                const int64_t ix = cell % k, iy = (cell / k) % k, iz = cell / ((int64_t)k * k);
+                if (!c->occ[((iz / B) * nb + iy / B) * nb + ix / B]) continue;
+            }
+            n_look += 1;
+            const double sig = cache_sigma(c, wc[j]);
+            if (!(sig > 0.0)) continue;
+            n_occ += 1;
+            cache_uvw(c, wc[j], uvw);
+            double col[3];
+            for (int ch = 0; ch < 3; ++ch) {
+                double x = 0.0;
+                for (int q = 0; q < D; ++q) x += beta[q] * uvw[ch * D + q]; /* Eq. 5 */
+                col[ch] = p->act == ORC_ACT_IDENTITY ? x : 1.0 / (1.0 + exp(-x));
+            }
+            const double od = sig * (double)wd[j];
+            const double alpha = -expm1(-od); /* Eq. 1 */
+            for (int ch = 0; ch < 3; ++ch) C[ch] += T * alpha * col[ch];
+            T *= exp(-od);
+            const int64_t f = orc_fix((double)((float)sig * wd[j]));
+            S = (S > INT64_MAX - f) ? INT64_MAX : S + f;
+            if (S >= X->s_thr) {
+                n_steps = j + 1;
+                terminated = 1;
+                break;
+            }
+        }
+        if (cells)
+            for (int j = n_steps; j < N; ++j) cells[j] = terminated ? -2 : -1;
+        for (int ch = 0; ch < 3; ++ch) rgba[ch] = C[ch] + T * (double)p->bg[ch];
+        rgba[3] = 1.0 - T;
+        if (stats) {
+            stats[0] = n_steps;
+            stats[1] = n_look;
+            stats[2] = n_occ;
+            stats[3] = (int32_t)dcell;
+        }
+        return;
+    }
     /* Cell coordinates of sample i: g_a = (o_a + t_i d_a - bmin_a) s_a with
      * t_i = near + (i + 1/2) Delta, evaluated in binary32 as
      * g_a = fma(i + 1/2, e_a, f_a), e_a = (d_a s_a) Delta,
@@ -482,6 +614,7 @@ int orc_render_pixels(const orc_cache *c, const orc_camera *cam, const orc_param
                       const int32_t *px, const int32_t *py, double *rgba, int32_t *stats, int32_t *cells,
                       int nthreads) {
     if (c->k <= 0 || c->D < 1 || c->D > 16 || c->l < 1 || p->N < 1 || nthreads < 1) return -1;
+    if (p->voxels && p->N > FNR_ORC_MAX_N) return -1;
     if (p->skip_empty && (!c->occ || c->occ_brick < 1)) return -1;
     float *tab = (float *)malloc(sizeof(float) * (size_t)c->l * 2);
     if (!tab) return -1;
@@ -489,7 +622,7 @@ int orc_render_pixels(const orc_cache *c, const orc_camera *cam, const orc_param
     ray_ctx X;
     X.c = c; X.cam = cam; X.p = p; X.ct = tab; X.qp = tab + c->l;
     X.dt = orc_dt(p->t_near, p->t_far, p->N);
-    X.s_thr = orc_s_thr(p->t_thr, X.dt);
+    X.s_thr = orc_s_thr(p->t_thr, p->voxels ? 1.0f : X.dt); /* voxels: the optical depth is sum sigma delta */
     for (int a = 0; a < 3; ++a) X.scale[a] = (float)((double)c->k / ((double)c->bmax[a] - (double)c->bmin[a]));
     job_t *jobs = (job_t *)malloc(sizeof(job_t) * (size_t)nthreads);
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);

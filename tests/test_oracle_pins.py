@@ -608,3 +608,129 @@ def test_uncached_render_homogeneous_closed_form(round_bf16):
         q = o[None, :] + t[:, None] * d[None, :]
         exact = int(((q >= -1.5) & (q < 1.5)).all(axis=1).sum())
         assert abs(exact - int(n_in[r])) <= 1
+
+
+# ------------------------------------------------------------------ voxel walk (Section 4: every voxel visited)
+def _slab_cells_fp64(k, o, d, t_near, t_far, bmin=(-1.5, -1.5, -1.5), bmax=(1.5, 1.5, 1.5)):
+    """Brute force: every cell's parameter interval on the ray, FP64 slabs in world units."""
+    o = np.asarray(o, dtype=np.float64)
+    d = np.asarray(d, dtype=np.float64)
+    lo_b = np.asarray(bmin, dtype=np.float64)
+    h = (np.asarray(bmax, dtype=np.float64) - lo_b) / k
+    out = []
+    for iz in range(k):
+        for iy in range(k):
+            for ix in range(k):
+                c = np.array([ix, iy, iz], dtype=np.float64)
+                t0, t1 = t_near, t_far
+                for a in range(3):
+                    b0, b1 = lo_b[a] + c[a] * h[a], lo_b[a] + (c[a] + 1) * h[a]
+                    if d[a] == 0.0:
+                        if not (b0 <= o[a] < b1):
+                            t0, t1 = 1.0, 0.0
+                        continue
+                    ta, tb = (b0 - o[a]) / d[a], (b1 - o[a]) / d[a]
+                    t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+                if t1 > t0:
+                    out.append((t0, t1 - t0, (iz * k + iy) * k + ix))
+    out.sort()
+    return out
+
+
+@pytest.mark.parametrize("k", [5, 7])
+def test_voxel_walk_vs_fp64_slabs(k):
+    """The walk visits exactly the cells the FP64 ray meets, in ray order, each with its FP64 length; cells
+    the ray only grazes (length < 1e-4, within rounding of a corner or an edge) may appear either way."""
+    rng = np.random.default_rng(k)
+    n_rays = 0
+    for trial in range(300):
+        if trial % 3 == 0:  # from inside the box
+            o = rng.uniform(-1.4, 1.4, 3)
+        else:
+            o = rng.normal(size=3)
+            o = 4.0 * o / np.linalg.norm(o)
+        d = rng.normal(size=3)
+        if trial % 10 == 1:
+            d[rng.integers(0, 3)] = 0.0  # a ray parallel to a face
+        d = d / np.linalg.norm(d)
+        o32, d32 = o.astype(np.float32), d.astype(np.float32)
+        t_near, t_far = (0.0, 10.0) if trial % 4 else (0.5, 3.5)
+        cells, delta = oracle.voxel_walk(k, o32, d32, t_near, t_far, 4 * k)
+        ref = _slab_cells_fp64(k, o32, d32, t_near, t_far)
+        big_ref = [(c, L) for _, L, c in ref if L > 1e-4]
+        big = [(c, float(dl)) for c, dl in zip(cells, delta) if dl > 1e-4]
+        assert [c for c, _ in big] == [c for c, _ in big_ref], (trial, cells, ref)
+        for (_, dl), (_, L) in zip(big, big_ref):
+            assert abs(dl - L) < 2e-5, (trial, dl, L)
+        assert abs(float(np.sum(delta[delta > 0], dtype=np.float64)) - sum(L for _, L, _ in ref)) < 5e-5
+        # consecutive cells are face neighbours (one step along one axis)
+        xyz = np.stack([cells % k, (cells // k) % k, cells // (k * k)], axis=1)
+        if len(cells) > 1:
+            assert np.all(np.abs(np.diff(xyz, axis=0)).sum(axis=1) == 1)
+        n_rays += len(cells) > 0
+    assert n_rays > 100
+
+
+@pytest.mark.parametrize("sigma0,t_thr", [(0.7, 0.0), (3.0, 0.0), (50.0, 1e-4), (9.0, 1e-3)])
+def test_voxel_homogeneous_box_closed_form(sigma0, t_thr):
+    """All cells sigma0, colour c, voxel walk: C = c (1 - e^{-sigma0 L}) + e^{-sigma0 L} bg with L the sum of the
+    cells' lengths (the FP64 chord through the box without termination); with termination the walk stops at
+    the first cell where sum floor(fp32(sigma0 delta) 2^32) >= ceil(ln(1/T_thr) 2^32)."""
+    k, D, l = 16, 1, 8
+    c = np.array([0.3, 0.5, 0.7], dtype=np.float32).astype(np.float64)
+    cache = const_cache(k, D, l, sigma0, c, [1.0])
+    cam = scenegen.cameras(5, 1, 24, 16)[0]
+    bg = np.array([0.9, 0.2, 0.4], dtype=np.float32).astype(np.float64)
+    N = 3 * k
+    p = oracle.params_struct(N, 2.0, 6.0, t_thr, tuple(bg), oracle.ACT_IDENTITY, voxels=True)
+    rgba, st, cells = oracle.render_image(cache, cam, p, want_cells=True)
+    s_thr = oracle.lib().orc_s_thr(t_thr, 1.0)
+    checked = 0
+    for py in range(0, 16, 3):
+        for px in range(0, 24, 3):
+            d, o = oracle.ray(cam, px, py)
+            wc, wd = oracle.voxel_walk(k, o, d, 2.0, 6.0, N)
+            m = len(wc)
+            if t_thr > 0:
+                S = 0
+                for j in range(len(wc)):
+                    S += oracle.lib().orc_fix(float(np.float32(np.float32(sigma0) * wd[j])))
+                    if S >= s_thr:
+                        m = j + 1
+                        break
+            assert st[py, px, 0] == m
+            assert np.array_equal(cells[py, px, :m], wc[:m])
+            L = float(np.sum(wd[:m][wd[:m] > 0], dtype=np.float64))
+            s0 = float(np.float32(sigma0))  # the stored binary32 density
+            TL = math.exp(-s0 * L)
+            np.testing.assert_allclose(rgba[py, px, :3], c * (1 - TL) + TL * bg, rtol=0, atol=1e-12)
+            if t_thr == 0.0 and m > 0:
+                chord = sum(Lc for _, Lc, _ in _slab_cells_fp64(k, o, d, 2.0, 6.0))
+                assert abs(L - chord) < 5e-5
+            if t_thr > 0 and m < len(wc):
+                assert TL < t_thr * (1 + 1e-6)
+                L_prev = float(np.sum(wd[:m - 1][wd[:m - 1] > 0], dtype=np.float64))
+                assert math.exp(-s0 * L_prev) >= t_thr * (1 - 1e-6)
+            checked += m > 0
+    assert checked > 10
+
+
+def test_voxel_skip_and_empty(tiny_workload, tiny_arrays):
+    """Voxel walk: skipping empty bricks changes only the lookup count; an empty cache gives T = 1 and C = bg."""
+    w = tiny_workload
+    sig, uvw, beta = tiny_arrays
+    cache = oracle.quantize_cache(w.k, w.D, w.l, sig, uvw, beta, oracle.FP32, oracle.FP32).set_occupancy(4)
+    cam = w.cameras()[0]
+    N = 3 * w.k
+    p = oracle.params_struct(N, voxels=True)
+    ps = oracle.params_struct(N, voxels=True, skip_empty=True)
+    a = oracle.render_image(cache, cam, p, want_cells=True)
+    b = oracle.render_image(cache, cam, ps, want_cells=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    assert np.array_equal(a[1][..., [0, 2, 3]], b[1][..., [0, 2, 3]])
+    assert (b[1][..., 1] <= a[1][..., 1]).all() and (b[1][..., 1] < a[1][..., 1]).any()
+    assert (a[1][..., 2] > 0).any()
+    empty = oracle.quantize_cache(w.k, w.D, w.l, np.zeros_like(sig), uvw, beta, oracle.FP32, oracle.FP32)
+    r = oracle.render_image(empty, cam, oracle.params_struct(N, bg=(0.25, 0.5, 1.0), voxels=True))
+    assert np.all(r[0][..., :3] == np.array([0.25, 0.5, 1.0], np.float32)) and np.all(r[0][..., 3] == 0)
+    assert np.all(r[1][..., 2] == 0)
