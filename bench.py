@@ -753,6 +753,40 @@ def run_fnr(args):
     fnr.fnr_cache_free(ctx, bcache)
     del rgba_skip, stats_skip, rgba_b
 
+    # the voxel walk (FNR_RENDER_VOXELS): every cell a ray passes through, N = 3k caps nothing
+    voxel_line = {}
+    for vskip in (False, True):
+        params_v = fnr.make_params(3 * w.k, w.t_near, w.t_far, w.t_thr, w.bg, skip_empty=vskip, voxels=True)
+        rgba_v = torch.empty_like(rgba)
+        stats_v = torch.empty_like(stats)
+        for i in range(w.n_cams):
+            fnr.fnr_render(ctx, cache, [fcams[i]], params_v, rgba_v[i], stats_v[i], stream=stream)
+        torch.cuda.synchronize()
+        st_v = stats_v.cpu().numpy().reshape(w.n_cams, w.H, w.W, 4)
+        alg_v = float(np.mean([algorithmic_bytes(st_v[i], w.D, 4, 4, 4) for i in range(w.n_cams)]))
+        if vskip:
+            alg_v += occ_bytes
+        v_steps = max(3, args.steps // 20)
+        for _ in range(2):
+            for i in range(w.n_cams):
+                fnr.fnr_render(ctx, cache, [fcams[i]], params_v, rgba_v[i], None, stream=stream)
+        k0.record(stream)
+        for s_ in range(v_steps):
+            for i in range(w.n_cams):
+                fnr.fnr_render(ctx, cache, [fcams[i]], params_v, rgba_v[i], None, stream=stream)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        v_ms = k0.elapsed_time(k1) / (v_steps * w.n_cams)
+        voxel_line["skip_empty" if vskip else "plain"] = {
+            "mrays_per_s": npix / (v_ms * 1e-3) / 1e6, "launch_ms": v_ms,
+            "cells_per_ray": float(st_v[..., 0].mean()), "lookups_per_ray": float(st_v[..., 1].mean()),
+            "occupied_per_ray": float(st_v[..., 2].mean()),
+            "roofline_frac": alg_v / (v_ms * 1e-3) / 1e9 / float(measured_peaks()[0]["hbm_gbs"]),
+            "algorithmic_bytes_per_launch": alg_v}
+        del rgba_v, stats_v
+    voxel_line["n_samples"] = 3 * w.k
+    voxel_line["bytes"] = "densities looked up + records of composited cells + beta + RGBA (+ brick bits)"
+
     # the same 8 views in one launch (fnr_render takes several cameras): no per-launch tail
     for _ in range(3):
         fnr.fnr_render(ctx, cache, fcams, params, rgba.view(-1), None, stream=stream)
@@ -798,6 +832,7 @@ def run_fnr(args):
                              "algorithmic_bytes_per_launch": alg_skip,
                              "bytes": "densities looked up + records of occupied samples + beta + RGBA + brick bits"}},
             "bricks_layout": bricks_line,
+            "voxel_walk": voxel_line,
             "all_views_one_launch": {
                 "mrays_per_s": w.n_cams * npix / (mv_ms * 1e-3) / 1e6, "launch_ms": mv_ms,
                 "roofline_frac": alg_per_launch * w.n_cams / (mv_ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"])},

@@ -281,6 +281,37 @@ typedef struct {
  * binary32 atan2f values, so colours differ from an FP64 evaluation by up to
  * ~1e-4 rather than 1e-5; dir_cell still reports the nearest bin. */
 #define FNR_RENDER_DIR_BILINEAR 2u
+/* Voxel walk (the paper integrates every voxel a ray passes through once the
+ * ray has reached the density, Section 4): instead of N uniform samples, each
+ * cell the ray passes through is one sample whose delta is the ray's length
+ * inside the cell. The cells of the segment [t0, t1] = [max(t_near, t_enter),
+ * min(t_far, t_exit)] inside the box are walked in order, in binary32 with
+ * this sequence, in grid units g_a(t) = t u_a + w_a:
+ *   u_a = d_a s_a, w_a = (o_a - bmin_a) s_a (s_a = k / (bmax_a - bmin_a) in
+ *     binary32, the cache's scale; o, d from the fixed ray sequence);
+ *   box: for u_a != 0 the entry / exit times are -w_a / u_a and (k - w_a) / u_a
+ *     (the smaller enters); u_a == 0 needs 0 <= w_a < k; t0 = the largest
+ *     entry and t_near, t1 = the smallest exit and t_far; no cells unless
+ *     t0 < t1;
+ *   start cell c_a = floor(fma(t0, u_a, w_a)) clamped to [0, k - 1];
+ *   next crossing along a: ((c_a + 1) - w_a) / u_a (u_a > 0), (c_a - w_a) / u_a
+ *     (u_a < 0), +infinity (u_a == 0);
+ *   per cell: a* = the axis with the smallest crossing (x, then y, then z on
+ *     ties), t_next its crossing, delta = min(t_next, t1) - t (t = t0 at the
+ *     start); the walk ends after this cell unless t_next < t1; t = max(t,
+ *     t_next); c_a* moves one cell and the walk ends if it leaves [0, k);
+ *     otherwise a*'s crossing is recomputed.
+ * A cell with delta <= 0 (rounding at a corner) is visited without a lookup.
+ * n_samples caps the walk (n_samples >= 3k never cuts a ray short). Eq. 1 per
+ * cell with delta_i = delta; termination when sum floor(fp32(sigma delta) 2^32)
+ * >= ceil(ln(1/T_thr) 2^32). Stats: n_steps = cells walked, n_lookups =
+ * density lookups (cells with delta > 0; with FNR_RENDER_SKIP_EMPTY those in
+ * occupied bricks), n_occupied = composited cells. debug cells: the walked
+ * cells in order, then -1 (walk ended) or -2 (terminated). Combines with
+ * FNR_RENDER_SKIP_EMPTY and FNR_RENDER_DIR_BILINEAR; dense caches only, and
+ * not for served requests, fnr_render_noalloc or fnr_render_mlp
+ * (FNR_ERR_UNSUPPORTED). */
+#define FNR_RENDER_VOXELS 4u
 
 typedef struct {
     int32_t n_steps;    /* samples visited (i + 1 of the terminating sample, else N) */

@@ -33,6 +33,7 @@ FNR_ACT_SIGMOID = 0
 FNR_ACT_IDENTITY = 1
 FNR_RENDER_SKIP_EMPTY = 1
 FNR_RENDER_DIR_BILINEAR = 2
+FNR_RENDER_VOXELS = 4
 FNR_LAYOUT_DENSE = 0
 FNR_LAYOUT_BRICKS = 1
 FNR_SRC_ARRAYS = 1
@@ -301,12 +302,14 @@ def make_camera(cam: dict) -> fnr_camera:
 
 
 def make_params(n_samples, t_near=2.0, t_far=6.0, t_thr=1e-4, bg=(1.0, 1.0, 1.0),
-                activation=FNR_ACT_SIGMOID, skip_empty=False, dir_bilinear=False) -> fnr_render_params:
+                activation=FNR_ACT_SIGMOID, skip_empty=False, dir_bilinear=False, voxels=False) -> fnr_render_params:
+    """voxels: walk every cell the ray passes through (n_samples caps the walk; 3k covers any ray)."""
     p = fnr_render_params()
     p.n_samples, p.t_near, p.t_far, p.t_thr = int(n_samples), float(t_near), float(t_far), float(t_thr)
     p.bg[:] = [float(v) for v in bg]
     p.activation = int(activation)
-    p.flags = (FNR_RENDER_SKIP_EMPTY if skip_empty else 0) | (FNR_RENDER_DIR_BILINEAR if dir_bilinear else 0)
+    p.flags = ((FNR_RENDER_SKIP_EMPTY if skip_empty else 0) | (FNR_RENDER_DIR_BILINEAR if dir_bilinear else 0)
+               | (FNR_RENDER_VOXELS if voxels else 0))
     return p
 
 

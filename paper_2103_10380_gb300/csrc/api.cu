@@ -11,6 +11,9 @@
 
 namespace fnr {
 
+// The voxel walk's launcher (march_voxels.cu); r.dt carries t_far in that mode.
+cudaError_t launch_march_voxels(const MarchArgs &a, cudaStream_t s);
+
 static thread_local std::string g_last_error;
 
 fnr_status fail(fnr_status st, const char *fmt, ...) {
@@ -265,18 +268,22 @@ fnr_status make_render_const(const fnr_render_params *p, RenderConst *rc) {
     if (isnan(p->t_thr)) return fail(FNR_ERR_INVALID_ARG, "t_thr is NaN");
     if (p->activation != FNR_ACT_SIGMOID && p->activation != FNR_ACT_IDENTITY)
         return fail(FNR_ERR_INVALID_ARG, "unknown activation %d", p->activation);
-    if ((p->flags & ~(FNR_RENDER_SKIP_EMPTY | FNR_RENDER_DIR_BILINEAR)) != 0u)
+    if ((p->flags & ~(FNR_RENDER_SKIP_EMPTY | FNR_RENDER_DIR_BILINEAR | FNR_RENDER_VOXELS)) != 0u)
         return fail(FNR_ERR_INVALID_ARG, "unknown render flags 0x%x", p->flags);
     if (p->reserved != 0) return fail(FNR_ERR_INVALID_ARG, "reserved field must be 0");
+    const bool voxels = (p->flags & FNR_RENDER_VOXELS) != 0u;
     rc->N = p->n_samples;
     rc->t_near = p->t_near;
-    rc->dt = (p->t_far - p->t_near) / static_cast<float>(p->n_samples);
-    if (!(rc->dt > 0.0f)) return fail(FNR_ERR_INVALID_ARG, "sample spacing underflows");
+    // uniform samples: Delta; the voxel walk has no spacing and reads t_far from this field instead
+    rc->dt = voxels ? p->t_far : (p->t_far - p->t_near) / static_cast<float>(p->n_samples);
+    if (!voxels && !(rc->dt > 0.0f)) return fail(FNR_ERR_INVALID_ARG, "sample spacing underflows");
     rc->act = p->activation;
     if (!(p->t_thr > 0.0f)) {
         rc->s_thr = 0x7fffffffffffffffLL;
     } else {
-        const double v = ceil(log(1.0 / static_cast<double>(p->t_thr)) / static_cast<double>(rc->dt) * 4294967296.0);
+        // optical depth: Delta sum sigma (threshold divided by Delta) or, for the walk, sum sigma delta
+        const double per = voxels ? 1.0 : static_cast<double>(rc->dt);
+        const double v = ceil(log(1.0 / static_cast<double>(p->t_thr)) / per * 4294967296.0);
         rc->s_thr = v >= 9223372036854775807.0 ? 0x7fffffffffffffffLL : (v < 0.0 ? 0 : static_cast<long long>(v));
     }
     for (int c = 0; c < 3; ++c) rc->bg[c] = p->bg[c];
@@ -728,6 +735,8 @@ fnr_status fnr_render(fnr_context *ctx, const fnr_cache *cache, const fnr_camera
     RenderConst rc;
     fnr_status st = make_render_const(params, &rc);
     if (st != FNR_OK) return st;
+    if ((rc.flags & FNR_RENDER_VOXELS) && cache->view.layout != FNR_LAYOUT_DENSE)
+        return fail(FNR_ERR_UNSUPPORTED, "the voxel walk reads dense caches only");
     for (int i = 0; i < n_cams; ++i)
         if ((st = check_camera(&cams[i])) != FNR_OK) return st;
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -750,7 +759,8 @@ fnr_status fnr_render(fnr_context *ctx, const fnr_cache *cache, const fnr_camera
         }
         a.n_frames = nf;
         a.total_tiles = tiles;
-        if ((e = launch_march(a, s)) != cudaSuccess) return cuda_fail(e, "march launch");
+        if ((e = (rc.flags & FNR_RENDER_VOXELS) ? launch_march_voxels(a, s) : launch_march(a, s)) != cudaSuccess)
+            return cuda_fail(e, "march launch");
     }
     return FNR_OK;
 }

@@ -130,8 +130,9 @@ extern "C" fnr_status fnr_render_noalloc(const fnr_cache *cache, const fnr_camer
     if (st != FNR_OK) return st;
     if (cache->view.layout == FNR_LAYOUT_BRICKS)
         return fail(FNR_ERR_UNSUPPORTED, "fnr_render_noalloc reads dense caches (FNR_LAYOUT_DENSE)");
-    if (rc.flags & FNR_RENDER_SKIP_EMPTY)
-        return fail(FNR_ERR_UNSUPPORTED, "fnr_render_noalloc renders the plain path only (no FNR_RENDER_SKIP_EMPTY)");
+    if (rc.flags & (FNR_RENDER_SKIP_EMPTY | FNR_RENDER_VOXELS))
+        return fail(FNR_ERR_UNSUPPORTED,
+                    "fnr_render_noalloc renders the plain path only (no FNR_RENDER_SKIP_EMPTY or FNR_RENDER_VOXELS)");
     for (int i = 0; i < n_cams; ++i)
         if ((st = check_camera(&cams[i])) != FNR_OK) return st;
     const int prec = cache->desc.pos_precision, D = cache->desc.D;

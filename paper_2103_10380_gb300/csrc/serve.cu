@@ -560,6 +560,7 @@ fnr_status fnr_submit(fnr_context *ctx, const fnr_request *req, uint64_t *ticket
     r.req = *req;
     fnr_status st = make_render_const(&req->params, &r.rc);
     if (st != FNR_OK) return st;
+    if (r.rc.flags & FNR_RENDER_VOXELS) return fail(FNR_ERR_UNSUPPORTED, "served requests take uniform samples");
     if ((st = check_camera(&req->camera)) != FNR_OK) return st;
     const int D = req->cache->desc.D;
     r.key = serve_key(req->cache->desc.pos_precision, D, (r.rc.flags & FNR_RENDER_SKIP_EMPTY) != 0u,

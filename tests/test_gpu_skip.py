@@ -135,7 +135,7 @@ def test_invalid_flags_and_bricks(fnr, ctx, tiny_workload, tiny_arrays):
         cam = w.cameras()[0]
         out = torch.zeros(cam["W"] * cam["H"] * 4, device="cuda")
         p = fnr.make_params(w.n_samples)
-        p.flags = 4  # no such flag
+        p.flags = 8  # no such flag
         with pytest.raises(fnr.FnrError) as ei:
             fnr.fnr_render(ctx, cache, [cam], p, out)
         assert ei.value.status == fnr.FNR_ERR_INVALID_ARG
