@@ -417,8 +417,9 @@ struct Server {
                 continue;
             }
             // Completion words are polled, not waited on. While work is in flight,
-            // and for a short while after the last activity (requests tend to come
-            // in bursts), the thread spins; otherwise it sleeps until a submit.
+            // and for idle_spin_us after the last activity (requests tend to come
+            // in bursts; -1: always), the thread spins; otherwise it sleeps until a
+            // submit, and a request arriving then pays the thread's wake-up.
             if (busy || !pending.empty() || spin_forever || now - last_activity_ns < spin_after_ns) {
                 lk.unlock();
                 std::this_thread::yield();
