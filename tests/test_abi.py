@@ -99,3 +99,21 @@ def test_null_arguments_rejected_without_gpu(fnr):
     assert b"NULL" in L.fnr_last_error()
     assert L.fnr_render(None, None, None, 0, None, None, None, None, None) == fnr.FNR_ERR_INVALID_ARG
     assert L.fnr_context_destroy(None) == fnr.FNR_OK
+
+
+def test_binding_constants_match_header(fnr):
+    """Every integer constant the header defines (status codes, precisions, layouts, render flags,
+    limits) has the same value in the binding, and the binding defines no FNR_ constant the header
+    lacks; the render flags are distinct bits."""
+    src = open(os.path.join(ROOT, "include", "fnr.h")).read()
+    header = {n: int(v) for n, v in re.findall(r"^#define\s+(FNR_\w+)\s+(\d+)u?\s*(?:/\*.*)?$", src, re.M)}
+    assert len(header) >= 25
+    binding = {n: getattr(fnr, n) for n in dir(fnr) if n.startswith("FNR_") and isinstance(getattr(fnr, n), int)}
+    for n, v in binding.items():
+        assert n in header, f"{n} is not in fnr.h"
+        assert header[n] == v, f"{n}: header {header[n]}, binding {v}"
+    flags = [v for n, v in header.items() if n.startswith("FNR_RENDER_")]
+    assert all(f & (f - 1) == 0 for f in flags) and len(set(flags)) == len(flags)
+    for n in ("FNR_RENDER_SKIP_EMPTY", "FNR_RENDER_DIR_BILINEAR", "FNR_RENDER_VOXELS", "FNR_ERR_IO",
+              "FNR_LAYOUT_BRICKS"):
+        assert n in binding, n
