@@ -194,3 +194,27 @@ def test_voxel_scale_workload_sampled(fnr, ctx):
             assert np.all(st[..., 2] <= st[..., 1]) and np.all(st[..., 1] <= st[..., 0])
     finally:
         fnr.fnr_cache_free(ctx, cache)
+
+
+@pytest.mark.parametrize("prec,brick", [(0, 4), (1, 2), (2, 8)])
+def test_voxel_skip_without_cells(fnr, ctx, tiny_workload, tiny_arrays, prec, brick):
+    """Skipping without per-cell output leaves empty bricks in one step: the counters (n_steps counts every
+    cell of the jumped bricks) and colours must still equal the oracle's cell-by-cell walk."""
+    w = tiny_workload
+    sig, uvw, beta = tiny_arrays
+    cache = fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, prec, 1 if prec else 0, occupancy_brick=brick),
+                                sig.reshape(-1), uvw.reshape(-1), beta.reshape(-1))
+    try:
+        oc = oracle.quantize_cache(w.k, w.D, w.l, sig, uvw, beta, prec, 1 if prec else 0).set_occupancy(brick)
+        cams = [(w.cameras()[0], dict()), (w.cameras()[0], dict(t_thr=0.0)),
+                (scenegen.look_at_camera((0.1, 0.2, 0.3), 30, 20), dict(t_near=0.0, t_far=3.0)),
+                (scenegen.cameras(41, 1, 37, 29)[0], dict(t_thr=1e-3, t_near=3.0, t_far=4.5)),
+                (scenegen.cameras(43, 1, 29, 31)[0], dict())]
+        for cam, kw in cams:
+            for N in (3 * w.k, 50):
+                p = fnr.make_params(N, voxels=True, skip_empty=True, **kw)
+                got = render(fnr, ctx, cache, cam, p, with_cells=False)
+                ref = oracle.render_image(oc, cam, oparams(p))
+                check(got, ref, TOL)
+    finally:
+        fnr.fnr_cache_free(ctx, cache)
