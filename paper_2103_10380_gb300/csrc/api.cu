@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "fnr_internal.h"
+#include "nvtx_range.h"
 
 namespace fnr {
 
@@ -472,6 +473,7 @@ static fnr_status make_bricks(fnr_context *ctx, const fnr_cache *dense, const fn
 fnr_status fnr_build_cache(fnr_context *ctx, const fnr_cache_desc *desc, const fnr_cache_source *src,
                            fnr_stream_t stream, fnr_cache **out) {
     clear_error();
+    NvtxRange range("fnr_build_cache");
     if (!ctx || !desc || !src || !out) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     if (!desc_valid(desc)) return fail(FNR_ERR_INVALID_ARG, "invalid cache descriptor");
@@ -610,6 +612,7 @@ struct File {
 
 fnr_status fnr_cache_save(const fnr_cache *c, const char *path) {
     clear_error();
+    NvtxRange range("fnr_cache_save");
     if (!c || !path) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
     cudaError_t e = cudaSetDevice(c->ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
@@ -640,6 +643,7 @@ fnr_status fnr_cache_save(const fnr_cache *c, const char *path) {
 
 fnr_status fnr_cache_load(fnr_context *ctx, const char *path, fnr_stream_t stream, fnr_cache **out) {
     clear_error();
+    NvtxRange range("fnr_cache_load");
     if (!ctx || !path || !out) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     File F;
@@ -729,6 +733,7 @@ fnr_status fnr_render(fnr_context *ctx, const fnr_cache *cache, const fnr_camera
                       const fnr_render_params *params, float *rgba_dev, fnr_ray_stats *stats_dev,
                       int32_t *debug_cells_dev, fnr_stream_t stream) {
     clear_error();
+    NvtxRange range("fnr_render");
     if (!ctx || !cache || !cams || !rgba_dev) return fail(FNR_ERR_INVALID_ARG, "NULL argument");
     if (n_cams < 1) return fail(FNR_ERR_INVALID_ARG, "n_cams must be >= 1");
     if (!cache_belongs(ctx, cache)) return fail(FNR_ERR_INVALID_ARG, "cache does not belong to this context");

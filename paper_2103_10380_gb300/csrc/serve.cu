@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "march_device.cuh"
+#include "nvtx_range.h"
 
 namespace fnr {
 
@@ -284,6 +285,7 @@ struct Server {
     }
 
     fnr_status launch(Slot &s, int key, int total_tiles) {
+        NvtxRange range("fnr_serve_batch");
         ServeFn fn = serve_fn(key);
         const unsigned grid = unsigned((total_tiles + FNR_BLOCK / 32 - 1) / (FNR_BLOCK / 32));
         cudaError_t e;

@@ -10,6 +10,7 @@
 //     sigma and (u, v, w) from F_pos, Eq. 5 + activation, Eq. 1 and the exact
 //     integer termination; RGBA and counters.
 #include "march_device.cuh"
+#include "nvtx_range.h"
 
 namespace fnr {
 
@@ -199,6 +200,7 @@ extern "C" fnr_status fnr_render_mlp(fnr_context *ctx, const fnr_mlp *pos_mlp, c
                                      const fnr_render_params *params, float *rgba_dev, fnr_ray_stats *stats_dev,
                                      fnr_stream_t stream) {
     clear_error();
+    NvtxRange range("fnr_render_mlp");
     if (!ctx || !pos_mlp || !dir_mlp || !bmin || !bmax || !cam || !rgba_dev)
         return fail(FNR_ERR_INVALID_ARG, "NULL argument");
     if (D != 1 && D != 2 && D != 4 && D != 6 && D != 8 && D != 16)
