@@ -734,3 +734,28 @@ def test_voxel_skip_and_empty(tiny_workload, tiny_arrays):
     r = oracle.render_image(empty, cam, oracle.params_struct(N, bg=(0.25, 0.5, 1.0), voxels=True))
     assert np.all(r[0][..., :3] == np.array([0.25, 0.5, 1.0], np.float32)) and np.all(r[0][..., 3] == 0)
     assert np.all(r[1][..., 2] == 0)
+
+
+def test_voxel_walk_hand_cases():
+    """Walks worked out by hand in a k=4 box over [-1.5, 1.5)^3 (cells 0.75 wide): an axis-aligned ray, the
+    same ray cut by [t_near, t_far], a ray starting inside the box, one along -x, and one that misses."""
+    k = 4
+    idx = lambda x, y, z: (z * k + y) * k + x  # noqa: E731
+    # +z through x = y = 0 (cell 2 on both axes): enters at t = 3.5 (z = -1.5), four cells of 0.75
+    c, d = oracle.voxel_walk(k, [0.0, 0.0, -5.0], [0.0, 0.0, 1.0], 0.0, 10.0, 16)
+    assert list(c) == [idx(2, 2, z) for z in range(4)] and np.allclose(d, 0.75, atol=1e-6)
+    # the same ray on [4.0, 5.5]: z from -1.0 to 0.5 -> cells z = 0 (0.25 left), 1 (0.75), 2 (0.5)
+    c, d = oracle.voxel_walk(k, [0.0, 0.0, -5.0], [0.0, 0.0, 1.0], 4.0, 5.5, 16)
+    assert list(c) == [idx(2, 2, z) for z in range(3)] and np.allclose(d, [0.25, 0.75, 0.5], atol=1e-6)
+    # from inside the box at z = 0.1 (cell 2, exit at 0.75 after 0.65), one more cell to 1.5
+    c, d = oracle.voxel_walk(k, [0.2, -0.3, 0.1], [0.0, 0.0, 1.0], 0.0, 10.0, 16)
+    assert list(c) == [idx(2, 1, 2), idx(2, 1, 3)] and np.allclose(d, [0.65, 0.75], atol=1e-6)
+    # -x at y = z = -1.0 (cell 0): x from 1.5 down to -1.5, cells x = 3, 2, 1, 0
+    c, d = oracle.voxel_walk(k, [3.0, -1.0, -1.0], [-1.0, 0.0, 0.0], 0.0, 10.0, 16)
+    assert list(c) == [idx(x, 0, 0) for x in (3, 2, 1, 0)] and np.allclose(d, 0.75, atol=1e-6)
+    # parallel to the box outside it: no cells
+    c, d = oracle.voxel_walk(k, [2.0, 0.0, -5.0], [0.0, 0.0, 1.0], 0.0, 10.0, 16)
+    assert len(c) == 0
+    # the step cap
+    c, d = oracle.voxel_walk(k, [0.0, 0.0, -5.0], [0.0, 0.0, 1.0], 0.0, 10.0, 2)
+    assert list(c) == [idx(2, 2, 0), idx(2, 2, 1)]
