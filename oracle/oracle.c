@@ -20,7 +20,7 @@
  *   - Supplementary "Meshing & Rendering": Beer-Lambert extinction with early
  *     ray termination; here: stop after the first sample whose transmittance
  *     falls to T_thr, decided by an exact integer optical-depth sum.
- *   - Section 4 ("visiting every voxel"): the voxel walk, one sample per cell
+ *   - Section 4 (integration over every voxel on the ray): the voxel walk, one sample per cell
  *     the ray passes through with delta = the ray's length inside the cell
  *     (orc_voxel_walk).
  *   - Supplementary "Cache size calculation" (second version): dense cache
