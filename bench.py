@@ -121,7 +121,7 @@ def algorithmic_bytes(stats: np.ndarray, D: int, s_sigma: int, s_uvw: int, s_bet
 
 
 # DRAM bytes (read + write) of one plain FP32 march launch of the default workload, from one ncu capture
-# (profiles/march_fp32_k512_800x800_traffic.md); reported only while the kernel sources are unchanged.
+# (dram__bytes_read.sum + dram__bytes_write.sum); reported only while the kernel sources are unchanged.
 MARCH_TRAFFIC = {"sources_sha256": "19ee25ab1d8660dbfe2de8b77a67ce5ed24d22c85a3db3d06bbb04bd8b1bf71a",
                  "bytes_per_launch": 334.0e6, "k": 512}
 MARCH_SOURCES = ("march_device.cuh", "march.cu", "fnr_internal.h")

@@ -428,8 +428,10 @@ FNR_API fnr_status fnr_wait(fnr_context *ctx, uint64_t ticket, uint32_t timeout_
  * process exits. Views, caches and outputs are the caller's, laid out as for
  * fnr_render; done_words (nullable; device-visible, e.g. host-mapped) gets 1
  * in word f when view f is finished. Stream-ordered on `stream`.
- * The first call on a device looks up the array's device address (with that
- * device current), so make that first call before any stream capture. Every
+ * Every call looks up the array's device address with the device current (a
+ * context reset between calls therefore does no harm); the first call for a
+ * device and cache format also queries the kernel's occupancy, so make that
+ * first call before any stream capture. Every
  * call shares the array and clears the counters it uses before its launch:
  * calls whose launches overlap on the GPU race, so keep them on one stream or
  * order them. Errors: INVALID_ARG (more than 32 views: the scratch holds one

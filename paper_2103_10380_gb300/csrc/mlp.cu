@@ -31,9 +31,6 @@
 // The next layer's weights load while the epilogue runs. Every mbarrier wait
 // is bounded; a wait that runs out sets the error word and a CTA-wide abort
 // flag, every role leaves its loop, and the tensor memory is freed.
-// Optionally (FNR_MLP_CLUSTER > 1) clusters of CTAs share each weight chunk
-// through multicast bulk copies; measured no faster, so off by default.
-#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -52,12 +49,6 @@ constexpr int kTileM = 128;
 constexpr int kMaxK = 256;
 constexpr int kMaxN = 256;
 constexpr int kChunkK = 64;                          // K columns per weight chunk: one 128-byte swizzle row
-// FNR_MLP_CLUSTER: CTAs per thread-block cluster; each CTA loads 1/n of every
-// weight chunk and multicasts it to the cluster, so the L2 serves each chunk
-// once per cluster instead of once per CTA
-#ifndef FNR_MLP_CLUSTER
-#define FNR_MLP_CLUSTER 1
-#endif
 #ifndef FNR_MLP_SLOTS
 #define FNR_MLP_SLOTS 2
 #endif
@@ -68,7 +59,6 @@ constexpr int kChunkK = 64;                          // K columns per weight chu
 #define FNR_MLP_BIAS_SMEM 0
 #endif
 constexpr int kSlots = FNR_MLP_SLOTS;                // ring slots
-constexpr int kCluster = FNR_MLP_CLUSTER;            // CTAs sharing each weight chunk
 constexpr int kSlotBytes = kMaxN * kChunkK * 2;      // 32 KB
 constexpr int kPair = FNR_MLP_PAIR;                  // tiles in flight per CTA
 #ifndef FNR_MLP_FIRST_EPI
@@ -175,17 +165,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
-// The same, one slice multicast to the CTAs of the cluster in cta_mask (same
-// shared-memory offsets; each destination's mbarrier receives the slice's bytes).
-__device__ __forceinline__ void bulk_g2s_multicast(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
-                                                   uint16_t cta_mask) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
-        "%4;" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar), "h"(cta_mask)
-        : "memory");
-}
-
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -230,14 +209,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
 
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// Commit that arrives on the mbarrier at this offset in every CTA of cta_mask.
-__device__ __forceinline__ void umma_commit_multicast(uint32_t bar, uint16_t cta_mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
-                     "r"(bar),
-                 "h"(cta_mask)
-                 : "memory");
 }
 
 // 16 columns of this warp's TMEM lane quarter, without waiting (see tmem_wait).
@@ -369,7 +340,7 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
     if (tid == 0) {
         for (int s = 0; s < kSlots; ++s) {
             mbar_init(full_bar(s), 1);
-            mbar_init(empty_bar(s), kCluster);  // one release per CTA of the cluster
+            mbar_init(empty_bar(s), 1);
         }
         for (int t = 0; t < kPair; ++t) {
             mbar_init(acc_full(t), 1);
@@ -390,20 +361,14 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    namespace cg = cooperative_groups;
-    const uint32_t crank = kCluster > 1 ? cg::this_cluster().block_rank() : 0u;
-    constexpr uint16_t kCtaMask = uint16_t((1u << kCluster) - 1u);
-    if (kCluster > 1) cg::this_cluster().sync();  // every CTA's barriers exist before any multicast
     const uint32_t tmem = *tmem_slot;
     // Tiles go to CTAs in groups of kPair: group r holds tiles (kPair r + t) * grid + bid, t < kPair;
     // a tile past the end is carried as an empty one (no outputs).
     const long long n_tiles = (A.n_points + kTileM - 1) / kTileM;
     const long long G = gridDim.x;
     auto pair_tile = [&](long long r, int t) { return (kPair * r + t) * G + blockIdx.x; };
-    // the same count for every CTA of a cluster (they share the weight stream); the cluster's first
-    // CTA has the most tiles, the others carry empty ones
-    const long long bid0 = (long long)blockIdx.x - crank;
-    const long long n_pairs = n_tiles > bid0 ? (n_tiles - bid0 + kPair * G - 1) / (kPair * G) : 0;
+    const long long bid = blockIdx.x;
+    const long long n_pairs = n_tiles > bid ? (n_tiles - bid + kPair * G - 1) / (kPair * G) : 0;
     // a warp-wide bounded wait (lane 0 polls); false when it ran out or another role aborted
     auto warp_wait = [&](uint32_t bar, uint32_t parity) {
         int ok = 1;
@@ -428,20 +393,9 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                             const uint32_t bytes = uint32_t(Ly.N) * uint32_t(kChunkK) * 2u;
                             mbar_expect_tx(full_bar(slot), bytes);
                             const char *src = reinterpret_cast<const char *>(Ly.w) + size_t(c) * Ly.N * kChunkK * 2;
-                            if (kCluster == 1) {
-                                bulk_g2s(smem_u32(ring) + uint32_t(slot) * kSlotBytes, src, bytes, full_bar(slot));
-                            } else {  // this CTA's slice, to every CTA of the cluster
-                                const uint32_t part = bytes / kCluster;
-                                bulk_g2s_multicast(smem_u32(ring) + uint32_t(slot) * kSlotBytes + crank * part,
-                                                   src + crank * part, part, full_bar(slot), kCtaMask);
-                            }
+                            bulk_g2s(smem_u32(ring) + uint32_t(slot) * kSlotBytes, src, bytes, full_bar(slot));
                         }
                     }
-            // Every CTA of the cluster has released the last use of each slot, so no
-            // release (a remote mbarrier arrive) is still travelling here at exit.
-            if (kCluster > 1)
-                for (long long j = it > kSlots ? it - kSlots : 0; j < it && !abort_flag; ++j)
-                    if (!mbar_wait(empty_bar(int(j % kSlots)), uint32_t((j / kSlots) & 1), A.err, &abort_flag)) break;
         }
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
@@ -471,8 +425,7 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                                     smem_desc_sw128(smem_u32(ring) + uint32_t(slot) * kSlotBytes + uint32_t(s) * 32u);
                                 umma_bf16(d_tmem, ad, bd, idesc, (c > 0 || s > 0) ? 1u : 0u);
                             }
-                            if (kCluster == 1) umma_commit(empty_bar(slot));
-                            else umma_commit_multicast(empty_bar(slot), kCtaMask);
+                            umma_commit(empty_bar(slot));
                         }
                         if (abort_flag) break;
                         if (li == 0) umma_commit(enc_free(t));  // the staging buffer may be refilled
@@ -641,7 +594,6 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
         }
     }
     __syncthreads();
-    if (kCluster > 1) cg::this_cluster().sync();  // no CTA leaves while a peer may still address it
     if (warp == kMmaWarp) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
@@ -745,33 +697,8 @@ fnr_status mlp_launch(const fnr_mlp *m, MlpArgs &A, int num_sms, cudaStream_t s)
         cudaSuccess)
         return cuda_fail(e, "MLP smem attribute");
     const long long tiles = (A.n_points + kTileM - 1) / kTileM;
-    if (kCluster == 1) {
-        const int grid = int(tiles < num_sms ? tiles : num_sms);
-        mlp_kernel<<<grid, kThreads, kSmemBytes, s>>>(A);
-    } else {
-        // one CTA per SM: as many whole clusters as fit at once, no more than the tiles need
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = kCluster;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = kSmemBytes;
-        cfg.stream = s;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cfg.gridDim = dim3(unsigned(num_sms / kCluster * kCluster));
-        int max_clusters = 0;
-        if ((e = cudaOccupancyMaxActiveClusters(&max_clusters, mlp_kernel, &cfg)) != cudaSuccess)
-            return cuda_fail(e, "MLP cluster occupancy");
-        if (max_clusters < 1) return fail(FNR_ERR_UNSUPPORTED, "MLP kernel: no cluster of %d CTAs fits", kCluster);
-        long long clusters = (tiles + kCluster - 1) / kCluster;
-        if (clusters > max_clusters) clusters = max_clusters;
-        cfg.gridDim = dim3(unsigned(clusters * kCluster));
-        e = cudaLaunchKernelEx(&cfg, mlp_kernel, A);
-        if (e != cudaSuccess) return cuda_fail(e, "MLP launch");
-    }
+    const int grid = int(tiles < num_sms ? tiles : num_sms);
+    mlp_kernel<<<grid, kThreads, kSmemBytes, s>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "MLP launch");
     int herr = 0;
     if ((e = cudaMemcpyAsync(&herr, ebuf.p, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||

@@ -45,7 +45,6 @@ static_assert(kNoAllocMaxViews <= kMaxFramesPerLaunch, "views are passed by valu
 static __device__ __align__(256) unsigned int g_noalloc_scratch[kNoAllocScratchWords];
 
 std::mutex g_setup_mu;
-unsigned int *g_scratch_ptr[kMaxDevices] = {};
 int g_grid[kMaxDevices][3][17] = {};
 
 template <int PREC, int D>
@@ -140,20 +139,18 @@ extern "C" fnr_status fnr_render_noalloc(const fnr_cache *cache, const fnr_camer
     if (!fn) return fail(FNR_ERR_UNSUPPORTED, "fnr_render_noalloc supports D in {1,2,3,4,6,8,12,16}, got %d", D);
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    // The device address of the static scratch, asked for on every call with the
+    // device current (host code cannot use the array's name as a device
+    // address). Asking again each time costs no allocation, and it stays right
+    // if the caller has reset the device's primary context since the last call.
     unsigned int *scratch = nullptr;
+    if ((e = cudaGetSymbolAddress(reinterpret_cast<void **>(&scratch), g_noalloc_scratch)) != cudaSuccess)
+        return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
     int grid = 0;
     {
-        // One-time set-up per device, done by the first call on that device
-        // (with the device current): the device address of the static scratch
-        // and the persistent grid size of each kernel instance.
+        // One-time set-up per device and kernel instance, done by the first call
+        // that needs it: the persistent grid size (an occupancy query).
         std::lock_guard<std::mutex> g(g_setup_mu);
-        if (!g_scratch_ptr[device]) {
-            unsigned int *p = nullptr;
-            if ((e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_noalloc_scratch)) != cudaSuccess)
-                return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
-            g_scratch_ptr[device] = p;
-        }
-        scratch = g_scratch_ptr[device];
         if (!g_grid[device][prec][D]) {
             int per_sm = 0;
             if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(fn),

@@ -198,8 +198,8 @@ def test_voxel_scale_workload_sampled(fnr, ctx):
 
 @pytest.mark.parametrize("prec,brick", [(0, 4), (1, 2), (2, 8)])
 def test_voxel_skip_without_cells(fnr, ctx, tiny_workload, tiny_arrays, prec, brick):
-    """Skipping without per-cell output leaves empty bricks in one step: the counters (n_steps counts every
-    cell of the jumped bricks) and colours must still equal the oracle's cell-by-cell walk."""
+    """Skipping without per-cell output: cells in empty bricks are walked one by one without a density
+    load; the counters (n_steps counts every walked cell) and colours must equal the oracle's walk."""
     w = tiny_workload
     sig, uvw, beta = tiny_arrays
     cache = fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, prec, 1 if prec else 0, occupancy_brick=brick),

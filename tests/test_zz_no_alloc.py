@@ -53,14 +53,14 @@ def render_both(fnr, ctx, cache, cams, params):
     return ref.cpu().numpy(), ref_st.cpu().numpy(), outs
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_noalloc_matches_fnr_render(fnr, prec):
     w = scenegen.tiny()
     sig, uvw = scenegen.fill_position_grid(w.scene, w.k)
     beta = scenegen.direction_grid(w.scene, w.l)
     ctx = fnr.fnr_context_create(0, 0)
     try:
-        cache = fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, prec, prec), sig.reshape(-1),
+        cache = fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, prec, min(prec, 1)), sig.reshape(-1),
                                     uvw.reshape(-1), beta.reshape(-1))
         cams = [w.cameras()[0]] + scenegen.cameras(21, 2, 45, 27)  # ragged sizes, three views in one launch
         params = fnr.make_params(w.n_samples)
