@@ -89,6 +89,7 @@ def lib():
         L.orc_dt.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int32]; L.orc_dt.restype = ctypes.c_float
         L.orc_s_thr.argtypes = [ctypes.c_float, ctypes.c_float]; L.orc_s_thr.restype = ctypes.c_int64
         L.orc_fix.argtypes = [ctypes.c_double]; L.orc_fix.restype = ctypes.c_int64
+        L.orc_round_bf16.argtypes = [ctypes.c_double]; L.orc_round_bf16.restype = ctypes.c_double
         L.orc_trace_fp64.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, P]
         L.orc_trace_fp64.restype = None
         L.orc_posenc.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P]
@@ -369,6 +370,12 @@ def dt(t_near, t_far, N) -> float:
 
 def s_thr(t_thr, dt_) -> int:
     return lib().orc_s_thr(t_thr, dt_)
+
+
+def round_bf16(x) -> np.ndarray:
+    """Each value rounded to binary32, then to bfloat16 (both round to nearest even), as FP64."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1)
+    return np.array([lib().orc_round_bf16(float(v)) for v in x])
 
 
 def fix(sigma: float) -> int:

@@ -726,8 +726,11 @@ void orc_posenc(int64_t n, int n_in, int L, const double *x, int n_out, double *
     }
 }
 
-static double round_bf16(double v) {
-    /* binary32 rounding first, then bf16 round-to-nearest-even of that value */
+/* Rounding of an activation as a bf16 tensor-core chain stores it: to binary32
+ * first (round to nearest even), then to bfloat16 (8 exponent bits, 7 fraction
+ * bits; round to nearest even on the 16 dropped bits). Infinities and NaN pass
+ * through unchanged. */
+double orc_round_bf16(double v) {
     float f = (float)v;
     if (isnan(f) || isinf(f)) return f;
     uint32_t u;
@@ -764,7 +767,7 @@ static void *mlp_worker(void *arg) {
     double *g = h + maxw;
     for (int64_t r = J->tid; r < J->n; r += J->nth) {
         int din = J->dims[0];
-        for (int j = 0; j < din; ++j) h[j] = J->round_mode ? round_bf16(J->in[r * din + j]) : J->in[r * din + j];
+        for (int j = 0; j < din; ++j) h[j] = J->round_mode ? orc_round_bf16(J->in[r * din + j]) : J->in[r * din + j];
         for (int L = 0; L < J->n_layers; ++L) {
             int di = J->dims[L], dout = J->dims[L + 1];
             for (int o = 0; o < dout; ++o) {
@@ -773,7 +776,7 @@ static void *mlp_worker(void *arg) {
                 for (int i = 0; i < di; ++i) acc += w[i] * h[i];
                 if (L + 1 < J->n_layers) {
                     acc = acc > 0.0 ? acc : 0.0;
-                    if (J->round_mode) acc = round_bf16(acc);
+                    if (J->round_mode) acc = orc_round_bf16(acc);
                 }
                 g[o] = acc;
             }

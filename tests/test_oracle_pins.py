@@ -85,20 +85,47 @@ def test_homogeneous_box_closed_form(sigma0, expect_steps):
     if expect_steps is not None:
         assert n_steps == expect_steps
     assert st[0, 1] == m and st[0, 2] == m
-    # cells along the optical axis: x = y = 0 -> index 32; z from the exact sample depth
+
+
+@pytest.mark.parametrize("sigma0", [2.0, 50.0])
+def test_homogeneous_box_cells_single_answer(sigma0):
+    """Every sample's cell, worked out by hand, with no sample near a cell face.
+
+    Camera with the identity rotation (looking down -z) at eye = (0.01, -0.02, 4 + 1/128); the central
+    pixel's ray is d = (0, 0, -1) exactly. Sample i lies at t_i = 2 + (2i + 1)/32, so
+    z_i + 1.5 = (445 - 8i)/128 and the exact grid coordinate is gz_i = (445 - 8i)/6, which is never within
+    1/6 of an integer (445 - 8i is odd and not divisible by 3 for any i; 445 - 8i = 1 - 2i mod 6).
+    gx = 1.51 * 64/3 = 32.21 and gy = 1.48 * 64/3 = 31.57 are 0.2 cells or more from a face. So each
+    sample has exactly one correct cell: (floor(gz_i) * 64 + 31) * 64 + 32 for i = 8..55, outside the box
+    (-1) otherwise, -2 after termination. The colour is the closed form of the homogeneous box.
+    """
+    k, D, l, N = 64, 1, 8, 64
+    c = np.array([0.3, 0.5, 0.7], dtype=np.float32).astype(np.float64)
+    cache = const_cache(k, D, l, sigma0, c, [1.0])
+    cam = dict(c2w=np.array([1, 0, 0, 0.01, 0, 1, 0, -0.02, 0, 0, 1, 4 + 1 / 128], np.float32),
+               fx=np.float32(80.0), fy=np.float32(80.0), cx=np.float32(32.5), cy=np.float32(32.5), W=64, H=64)
+    d, _ = oracle.ray(cam, 32, 32)
+    assert list(d) == [0.0, 0.0, -1.0]
+    bg = (0.9, 0.2, 0.4)
+    p = oracle.params_struct(N, 2.0, 6.0, 1e-4, bg, oracle.ACT_IDENTITY)
+    rgba, st, cells = oracle.render_pixels(cache, cam, p, [32], [32], want_cells=True)
+    delta = 4.0 / N
+    m_thr = math.ceil(math.log(1e4) / (sigma0 * delta))
+    m = min(48, m_thr)
+    n_steps = 8 + m if m_thr <= 48 else N
+    assert st[0, 0] == n_steps and st[0, 1] == m and st[0, 2] == m
+    Tm = math.exp(-sigma0 * m * delta)
+    expect = c * (1 - Tm) + Tm * np.array(bg, dtype=np.float32).astype(np.float64)
+    np.testing.assert_allclose(rgba[0, :3], expect, rtol=0, atol=1e-12)
     for i in range(N):
-        z = 2 - (i + 0.5) / 16
         if i >= n_steps:
-            assert cells[0, i] == -2
+            want = -2
         elif i < 8 or i > 55:
-            assert cells[0, i] == -1
+            want = -1
         else:
-            gz = (z + 1.5) * 64 / 3  # exact: z is a multiple of 1/32
-            iz = math.floor(gz)
-            ok = {(iz * k + 32) * k + 32}
-            if abs(gz - round(gz)) < 1e-9:  # sample exactly on a cell face: binary32 rounding picks a side
-                ok.add(((round(gz) - 1) * k + 32) * k + 32)
-            assert cells[0, i] in ok
+            assert (445 - 8 * i) % 6 != 0
+            want = (((445 - 8 * i) // 6) * k + 31) * k + 32
+        assert cells[0, i] == want, (i, cells[0, i], want)
 
 
 def test_homogeneous_box_chord_form():
@@ -384,6 +411,124 @@ def test_mlp_forward_vs_numpy():
     # bf16 rounding mode stays within bf16 error of the exact chain
     hb = oracle.mlp_forward(Ws, bs, x, True)
     assert np.max(np.abs(hb - h)) < 0.05 * np.max(np.abs(h))
+
+
+def test_round_bf16_vs_torch_and_by_hand():
+    """The oracle's activation rounding: binary32 first, then bfloat16, both round to nearest even.
+
+    Hand-worked values near 1 (bf16 spacing 2^-7 there): 1 + 2^-8 is a tie between 1 and 1 + 2^-7 and goes
+    to the even 1; 1 + 3 * 2^-8 is a tie between 1 + 2^-7 and 1 + 2^-6 and goes to the even 1 + 2^-6;
+    1 + 2^-8 + 2^-20 lies above the tie and rounds up. An FP64 value first rounds to binary32, so
+    1 + 2^-8 + 2^-40 becomes the tie 1 + 2^-8 and then 1 (direct rounding would give 1 + 2^-7).
+    Then bit-for-bit against torch's float32 -> bfloat16 cast on random values, ties and subnormals."""
+    torch = pytest.importorskip("torch")
+    hand = [(1 + 2 ** -8, 1.0), (1 + 3 * 2 ** -8, 1 + 2 ** -6), (1 + 2 ** -8 + 2 ** -20, 1 + 2 ** -7),
+            (-(1 + 3 * 2 ** -8), -(1 + 2 ** -6)), (1 + 2 ** -8 + 2 ** -40, 1.0), (2 ** -130, 2 ** -130),
+            (3.0 * 2 ** -133 + 2 ** -149, 3.0 * 2 ** -133), (0.1, 0.10009765625), (-0.0, -0.0), (65504.0, 65536.0)]
+    got = oracle.round_bf16([v for v, _ in hand])
+    for (v, want), g in zip(hand, got):
+        assert g == want and math.copysign(1, g) == math.copysign(1, want), (v, g, want)
+    rng = np.random.default_rng(5)
+    mant = rng.integers(0, 2 ** 23, 4000, dtype=np.uint32)
+    expo = rng.integers(1, 255, 4000, dtype=np.uint32)
+    sign = rng.integers(0, 2, 4000, dtype=np.uint32)
+    bits = (sign << 31) | (expo << 23) | mant
+    ties = (bits & ~np.uint32(0xFFFF)) | np.uint32(0x8000)      # exactly halfway between two bf16 values
+    subn = rng.integers(1, 2 ** 23, 1000, dtype=np.uint32)      # binary32 subnormals
+    x = np.concatenate([bits, ties, subn]).view(np.float32)
+    ref = torch.from_numpy(x.copy()).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(oracle.round_bf16(x), ref)
+    special = oracle.round_bf16([np.inf, -np.inf, np.nan])
+    assert special[0] == np.inf and special[1] == -np.inf and np.isnan(special[2])
+
+
+def test_mlp_rounds_input_and_hidden_but_not_head():
+    """round_bf16 mode rounds the encoded input and every hidden activation to bf16, never the head's
+    outputs: with identity layers, input 1 + 2^-9 reaches the head as 1 (rounded), and a head bias of 2^-12
+    survives unrounded; the FP64 mode keeps everything."""
+    I2 = np.eye(2)
+    Ws, bs = [I2, I2], [np.zeros(2), np.array([2.0 ** -12, 0.0])]
+    x = np.array([[1 + 2 ** -9, 3.0]])
+    assert list(oracle.mlp_forward(Ws, bs, x, True)[0]) == [1 + 2 ** -12, 3.0]
+    assert list(oracle.mlp_forward(Ws, bs, x, False)[0]) == [1 + 2 ** -9 + 2 ** -12, 3.0]
+    # a hidden pre-activation that needs rounding: 1 + 2^-9 + 2^-9 = 1 + 2^-8 is a tie -> 1
+    Ws2 = [np.array([[1.0, 1.0]]), np.array([[1.0]])]
+    bs2 = [np.zeros(1), np.zeros(1)]
+    x2 = np.array([[1.0, 2.0 ** -8]])
+    assert oracle.mlp_forward(Ws2, bs2, x2, True)[0, 0] == 1.0
+
+
+def test_fp8_scale_and_codes_by_definition():
+    """Per-channel E4M3 quantisation (one binary32 scale per channel = absmax / 448, 1 for an all-zero
+    channel; q = E4M3(x / scale), nearest even, saturating; the density channel is clamped to >= 0 first).
+
+    Hand-worked channel {0, 1.5, -7, 3.5}: absmax 7, scale = 7/448 = 2^-6 exactly; x / scale =
+    {0, 96, -448, 224} -> codes {0x00, 0x6C (1.5 * 2^6: exponent field 13, mantissa 4), 0xFE (-448),
+    0x76 (1.75 * 2^7: exponent field 14, mantissa 6)}. As a density channel the -7 is clamped to 0 first:
+    absmax 3.5, scale 2^-7, codes {0x00, 0x74 (192), 0x00, 0x7E (448)}."""
+    ch = np.array([0.0, 1.5, -7.0, 3.5], np.float32)
+    s_u = oracle.fp8_scale(ch, False)
+    assert s_u == np.float32(7.0 / 448.0) == 2.0 ** -6
+    assert list(oracle.quantize_channel(oracle.FP8, ch, False, s_u)) == [0x00, 0x6C, 0xFE, 0x76]
+    s_s = oracle.fp8_scale(ch, True)
+    assert s_s == 2.0 ** -7
+    assert list(oracle.quantize_channel(oracle.FP8, ch, True, s_s)) == [0x00, 0x74, 0x00, 0x7E]
+    assert oracle.fp8_scale(np.zeros(5, np.float32), False) == 1.0
+    assert oracle.fp8_scale(np.array([-3.0, 0.0], np.float32), True) == 1.0  # clamped to all zero
+    # random channels: the absmax element encodes to +-448, nothing else saturates, and every code
+    # decodes to within half an E4M3 step of x / scale
+    rng = np.random.default_rng(3)
+    for trial in range(20):
+        x = (rng.standard_normal(500) * 10.0 ** rng.uniform(-3, 3)).astype(np.float32)
+        s = oracle.fp8_scale(x, False)
+        assert s == np.float32(np.float32(np.max(np.abs(x))) / np.float32(448.0))
+        q = oracle.quantize_channel(oracle.FP8, x, False, s)
+        a = int(np.argmax(np.abs(x)))
+        assert q[a] == (0xFE if x[a] < 0 else 0x7E)
+        y = (x / s).astype(np.float32).astype(np.float64)
+        assert np.all(np.abs(y) <= 448.0 * (1 + 2 ** -23))
+        dec = oracle.e4m3_decode(q)
+        step = np.where(np.abs(y) < 2 ** -6, 2.0 ** -9, 2.0 ** (np.floor(np.log2(np.maximum(np.abs(y), 2 ** -6))) - 3))
+        assert np.all(np.abs(dec - y) <= step / 2 * (1 + 1e-12))
+
+
+def test_fp8_cache_clamps_density_only():
+    """quantize_cache: the density plane is clamped before its scale is taken, the (u, v, w) channels are
+    not (their negative values set their scales and keep their sign); scales[0] belongs to the density."""
+    k, D, l = 2, 1, 2
+    sig = np.array([0, 1.5, -7, 3.5, 0, 0, 0, 0], np.float32)
+    uvw = np.zeros((8, 3), np.float32)
+    uvw[:4, 0] = [0, 1.5, -7, 3.5]
+    uvw[0, 1] = -2.0
+    beta = np.ones((l * l, D), np.float32)
+    q = oracle.quantize_cache(k, D, l, sig, uvw, beta, oracle.FP8, oracle.FP16)
+    assert q.scales[0] == 2.0 ** -7 and q.scales[1] == 2.0 ** -6
+    assert q.scales[2] == np.float32(2.0 / 448.0) and q.scales[3] == 1.0
+    assert list(np.asarray(q.sigma)[:4]) == [0x00, 0x74, 0x00, 0x7E]
+    qu = np.asarray(q.uvw).reshape(8, 3)
+    assert list(qu[:4, 0]) == [0x00, 0x6C, 0xFE, 0x76]
+    assert qu[0, 1] == 0xFE
+
+
+def test_build_sample_points_by_hand():
+    """The cache build evaluates F_pos at cell centres and F_dir at bin centres (Section 3.3; reading s5,
+    s15). k = 2 on [-1.5, 1.5]^3: centres +-0.75, cell (z*2 + y)*2 + x; k = 3: centres -1, 0, 1.
+    l = 2: theta centres pi/4, 3 pi/4 (from +z), phi centres pi/2, 3 pi/2; bin i_theta * 2 + i_phi."""
+    c = oracle.cell_centres(2, [0, 1, 2, 4, 7])
+    assert c.tolist() == [[-0.75, -0.75, -0.75], [0.75, -0.75, -0.75], [-0.75, 0.75, -0.75],
+                          [-0.75, -0.75, 0.75], [0.75, 0.75, 0.75]]
+    c3 = oracle.cell_centres(3, [0, 5, 13, 26])
+    np.testing.assert_allclose(c3, [[-1, -1, -1], [1, 0, -1], [0, 0, 0], [1, 1, 1]], atol=1e-15)
+    h = math.sqrt(0.5)
+    dirs = oracle.bin_directions(2, [0, 1, 2, 3])
+    np.testing.assert_allclose(dirs, [[0, h, h], [0, -h, h], [0, h, -h], [0, -h, -h]], atol=1e-15)
+    # each bin centre's direction is looked up in its own bin (the lookup is pinned against libm
+    # separately), for several resolutions
+    for l in (2, 3, 8, 64, 512):
+        bins = np.arange(l * l) if l <= 64 else np.random.default_rng(l).integers(0, l * l, 4000)
+        for b, d in zip(bins, oracle.bin_directions(l, bins)):
+            it, ip = oracle.dir_cell(l, d.astype(np.float32))
+            assert it * l + ip == b, (l, b, it, ip)
 
 
 def test_tabled_field_equals_dense(tiny_workload, tiny_arrays):
