@@ -44,6 +44,8 @@ def parse():
                     help="arrival window per request rate in the serving workload (its full length is 30)")
     ap.add_argument("--only-build", action="store_true",
                     help="time only the tensor-core cache build (F_pos over k^3, F_dir over 512^2)")
+    ap.add_argument("--check-points", type=int, default=1 << 20,
+                    help="random grid points of the built cache checked against the FP64 oracle (0: none)")
     ap.add_argument("--only-serve", action="store_true",
                     help="run only the serving workload (three resident k^3 scenes, Poisson arrivals)")
     return ap.parse_args()
@@ -331,9 +333,10 @@ def precision_config(fnr, torch, dev, repeats=5, pix_per_view=20000, rng_seed=7)
     return out
 
 
-def cache_build(fnr, torch, ctx, k=512, l=512):
+def cache_build(fnr, torch, ctx, k=512, l=512, check_points=1 << 20):
     """F_pos (8x256 ReLU + head, L=10) over k^3 cell centres and F_dir (4x128 ReLU + head, L=4) over l^2 bins,
-    bf16 on the tensor cores with fp32 accumulation; He-uniform weights, seed 0."""
+    bf16 on the tensor cores with fp32 accumulation; He-uniform weights, seed 0. The first build is also
+    checked against the FP64 oracle on check_points random grid points."""
     import scenegen
     pos = scenegen.mlp_weights(0, scenegen.FPOS_DIMS_D8)
     dirn = scenegen.mlp_weights(100, scenegen.FDIR_DIMS_D8)
@@ -343,20 +346,64 @@ def cache_build(fnr, torch, ctx, k=512, l=512):
     flops = flop_pt(scenegen.FPOS_DIMS_D8) * k ** 3 + flop_pt(scenegen.FDIR_DIMS_D8) * l * l
     desc = fnr.make_desc(k, 8, l)
     times = []
-    for _ in range(2):  # first call includes one-time set-up
+    for it in range(2):  # first call includes one-time set-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cache = fnr.fnr_build_cache_mlp(ctx, desc, pl, dl)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
+        if it == 0 and check_points:
+            error = build_error_vs_oracle(fnr, torch, cache, k, l, 8, pos, dirn, check_points)
         fnr.fnr_cache_free(ctx, cache)
     peaks, kind = measured_peaks()
     dt = min(times)
-    return {"workload": f"F_pos over {k}^3 + F_dir over {l}^2, bf16 x bf16 -> fp32", "flops": flops,
-            "seconds": dt, "tflops": flops / dt / 1e12, "peak_tflops": float(peaks["bf16_tflops"]),
-            "frac": flops / dt / 1e12 / float(peaks["bf16_tflops"]),
-            "peak_kind": f"{kind} cuBLAS bf16 (burst)",
-            "timing": "whole fnr_build_cache call (includes the cache allocation), best of 2"}
+    out = {"workload": f"F_pos over {k}^3 + F_dir over {l}^2, bf16 x bf16 -> fp32", "flops": flops,
+           "seconds": dt, "tflops": flops / dt / 1e12, "peak_tflops": float(peaks["bf16_tflops"]),
+           "frac": flops / dt / 1e12 / float(peaks["bf16_tflops"]),
+           "peak_kind": f"{kind} cuBLAS bf16 (burst)",
+           "timing": "whole fnr_build_cache call (includes the cache allocation), best of 2"}
+    if check_points:
+        out["error_vs_fp64_oracle"] = error
+    return out
+
+
+def build_error_vs_oracle(fnr, torch, cache, k, l, D, pos, dirn, n_points, seed=1):
+    """Error of a built cache against the FP64 oracle MLP (same bf16 weights, bf16 rounding of the input
+    and of every hidden activation) on n_points random grid cells (seed 1) and n_points / 16 random
+    direction bins, per output channel relative to the channel's rms: relative L2, max, and the fraction
+    of values within 1e-2 rms."""
+    import oracle
+    import scenegen
+    lay = fnr.fnr_cache_get_layout(cache)
+    rng = np.random.default_rng(seed)
+    cells = rng.integers(0, k ** 3, n_points)
+    bins = rng.integers(0, l * l, max(1, n_points // 16))
+
+    def dev_view(ptr, shape, typestr):
+        return torch.as_tensor(type("V", (), {"__cuda_array_interface__": {
+            "shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3}})(), device="cuda")
+
+    idx = torch.from_numpy(cells).cuda()
+    sig = dev_view(lay.sigma_dev, (k ** 3,), "<f4")[idx].cpu().numpy().astype(np.float64)
+    rec = dev_view(lay.uvw_dev, (k ** 3, lay.record_stride // 4), "<f4")[idx].cpu().numpy()
+    got = np.concatenate([sig[:, None], rec[:, :3 * D].astype(np.float64)], axis=1)
+    beta = dev_view(lay.beta_dev, (l * l, D), "<f4")[torch.from_numpy(bins).cuda()].cpu().numpy()
+    as64 = lambda L: [(scenegen.bf16_value(W).astype(np.float64), b.astype(np.float64)) for W, b in L]
+    t0 = time.perf_counter()
+    ref = oracle.mlp_eval(as64(pos), oracle.cell_centres(k, cells), 10, True)
+    ref[:, 0] = np.maximum(ref[:, 0], 0.0)
+    bref = oracle.mlp_eval(as64(dirn), oracle.bin_directions(l, bins), 4, True)
+    t_oracle = time.perf_counter() - t0
+
+    def stats(g, r):
+        rms = np.sqrt(np.mean(r ** 2, axis=0)) + 1e-12
+        e = np.abs(g - r) / rms
+        return {"rel_l2_max": float(np.sqrt(np.mean(e ** 2, axis=0)).max()), "max_over_rms": float(e.max()),
+                **{f"frac_within_{t:g}_rms_min": float(np.mean(e <= t, axis=0).min()) for t in (1e-2, 3e-2)}}
+
+    return {"f_pos": {"points": int(n_points), **stats(got, ref)},
+            "f_dir": {"points": int(bins.size), **stats(beta.astype(np.float64), bref)},
+            "oracle_seconds": t_oracle, "oracle_cores": os.cpu_count() or 1}
 
 
 def uncached_render(fnr, torch, dev, w, reps=3):
@@ -871,7 +918,8 @@ def main():
         import paper_2103_10380_gb300 as fnr
         torch.cuda.set_device(0)
         ctx = fnr.fnr_context_create(0, 0)
-        print(json.dumps({"cache_build": cache_build(fnr, torch, ctx, k=args.k)}), flush=True)
+        print(json.dumps({"cache_build": cache_build(fnr, torch, ctx, k=args.k, check_points=args.check_points)}),
+              flush=True)
         fnr.fnr_context_destroy(ctx)
         return
     if args.only_serve:

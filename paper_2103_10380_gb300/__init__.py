@@ -139,6 +139,8 @@ SIGNATURES = {
     "fnr_wait": ([_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(fnr_result)], ctypes.c_int32),
     "fnr_render_noalloc": ([_P, ctypes.POINTER(fnr_camera), ctypes.c_int32, ctypes.POINTER(fnr_render_params), _P,
                             _P, _P, _P], ctypes.c_int32),
+    "fnr_testing_fail_allocations": ([ctypes.c_int32, ctypes.c_int32], ctypes.c_int32),
+    "fnr_testing_mlp_fault": ([ctypes.c_int64, ctypes.c_int64], ctypes.c_int32),
 }
 
 _lib = None
@@ -389,3 +391,15 @@ def fnr_render_noalloc(cache: int, cams, params: fnr_render_params, rgba, stats=
     check(lib().fnr_render_noalloc(cache, arr, len(cams), ctypes.byref(params), rgba.data_ptr(),
                                    None if stats is None else stats.data_ptr(),
                                    None if done_words is None else done_words.data_ptr(), _stream_handle(stream)))
+
+
+# ------------------------------------------------------------------ failure injection (fnr_testing.h; tests only)
+def fnr_testing_fail_allocations(skip: int, count: int) -> None:
+    """The library's next `skip` device allocations succeed and the `count` after them fail (0 disarms)."""
+    check(lib().fnr_testing_fail_allocations(int(skip), int(count)))
+
+
+def fnr_testing_mlp_fault(wait_limit: int, withhold_chunk: int = -1) -> None:
+    """The next tensor-core build launch gives up its waits after wait_limit polls and, if withhold_chunk >= 0,
+    each CTA's producer withholds that weight chunk; the call then returns FNR_ERR_DEVICE."""
+    check(lib().fnr_testing_mlp_fault(int(wait_limit), int(withhold_chunk)))

@@ -167,7 +167,7 @@ static fnr_status build_from_arrays(fnr_cache *c, const fnr_cache_source *src, c
     const int64_t slab = dev ? k3 : std::max<int64_t>(1, std::min<int64_t>(k3, (int64_t(256) << 20) / (4 * (nch + 1))));
     DevBuf stage;
     if (!dev) {
-        if ((e = cudaMalloc(&stage.p, size_t(slab) * 4 * (nch + 1))) != cudaSuccess) return cuda_fail(e, "staging");
+        if ((e = dev_malloc(&stage.p, size_t(slab) * 4 * (nch + 1))) != cudaSuccess) return cuda_fail(e, "staging");
     }
     auto slab_ptrs = [&](int64_t c0, int64_t n, const float **sp, const float **up) -> cudaError_t {
         if (dev) {
@@ -186,7 +186,7 @@ static fnr_status build_from_arrays(fnr_cache *c, const fnr_cache_source *src, c
     };
     if (prec == FNR_PREC_FP8_E4M3) {
         DevBuf amax;
-        if ((e = cudaMalloc(&amax.p, sizeof(unsigned) * (1 + nch))) != cudaSuccess) return cuda_fail(e, "absmax");
+        if ((e = dev_malloc(&amax.p, sizeof(unsigned) * (1 + nch))) != cudaSuccess) return cuda_fail(e, "absmax");
         if ((e = cudaMemsetAsync(amax.p, 0, sizeof(unsigned) * (1 + nch), s)) != cudaSuccess)
             return cuda_fail(e, "memset");
         for (int64_t c0 = 0; c0 < k3; c0 += slab) {
@@ -218,7 +218,7 @@ static fnr_status build_from_arrays(fnr_cache *c, const fnr_cache_source *src, c
     const float *bp = src->beta;
     DevBuf bstage;
     if (!dev) {
-        if ((e = cudaMalloc(&bstage.p, size_t(nb) * 4)) != cudaSuccess) return cuda_fail(e, "beta staging");
+        if ((e = dev_malloc(&bstage.p, size_t(nb) * 4)) != cudaSuccess) return cuda_fail(e, "beta staging");
         if ((e = cudaMemcpyAsync(bstage.p, src->beta, size_t(nb) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return cuda_fail(e, "beta upload");
         bp = static_cast<const float *>(bstage.p);
@@ -428,7 +428,7 @@ static fnr_status make_bricks(fnr_context *ctx, const fnr_cache *dense, const fn
     c->footprint = L.total;
     c->n_bricks = uint64_t(n_bricks);
     c->ctx = ctx;
-    if ((e = cudaMalloc(&c->base, L.total)) != cudaSuccess) {
+    if ((e = dev_malloc(&c->base, L.total)) != cudaSuccess) {
         budget_uncharge(ctx, L.total);
         delete c;
         return cuda_fail(e, "brick cache allocation");
@@ -437,7 +437,7 @@ static fnr_status make_bricks(fnr_context *ctx, const fnr_cache *dense, const fn
     const char *dbase = static_cast<const char *>(dense->base);
     DevBuf slots;
     fnr_status st = FNR_OK;
-    if (n_bricks > 0 && (e = cudaMalloc(&slots.p, size_t(n_bricks) * 4)) != cudaSuccess) st = cuda_fail(e, "slots");
+    if (n_bricks > 0 && (e = dev_malloc(&slots.p, size_t(n_bricks) * 4)) != cudaSuccess) st = cuda_fail(e, "slots");
     if (st == FNR_OK &&
         ((n_bricks > 0 && (e = cudaMemcpyAsync(slots.p, slot_brick.data(), size_t(n_bricks) * 4,
                                                cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
@@ -512,7 +512,7 @@ fnr_status fnr_build_cache(fnr_context *ctx, const fnr_cache_desc *desc, const f
     c->desc = *desc;
     c->footprint = L.total;
     c->ctx = ctx;
-    if ((e = cudaMalloc(&c->base, L.total)) != cudaSuccess) {
+    if ((e = dev_malloc(&c->base, L.total)) != cudaSuccess) {
         budget_uncharge(ctx, L.total);
         delete c;
         return cuda_fail(e, "cache allocation");
@@ -672,7 +672,7 @@ fnr_status fnr_cache_load(fnr_context *ctx, const char *path, fnr_stream_t strea
     c->n_bricks = bricks ? h.n_bricks : 0;
     c->ctx = ctx;
     fnr_status st = FNR_OK;
-    if ((e = cudaMalloc(&c->base, L.total)) != cudaSuccess) {
+    if ((e = dev_malloc(&c->base, L.total)) != cudaSuccess) {
         budget_uncharge(ctx, L.total);
         delete c;
         return cuda_fail(e, "cache allocation");

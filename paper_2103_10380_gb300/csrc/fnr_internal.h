@@ -93,6 +93,16 @@ struct MarchArgs {
 };
 
 // Host-side helpers shared by the API and the kernels' launchers.
+// Every device allocation of the library goes through dev_malloc (testing.cu),
+// so the failure-injection hook of fnr_testing.h reaches all of them.
+cudaError_t dev_malloc(void **p, size_t bytes);
+template <class T>
+cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+// The armed cache-build fault (fnr_testing_mlp_fault), taken once: leaves the
+// arguments unchanged when none is armed.
+void take_mlp_fault(long long *wait_limit, long long *withhold);
 int rec_stride_bytes(int prec, int D);
 size_t elem_bytes(int prec);
 

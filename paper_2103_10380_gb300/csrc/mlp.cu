@@ -30,7 +30,9 @@
 //     stores by all sixteen warps.
 // The next layer's weights load while the epilogue runs. Every mbarrier wait
 // is bounded; a wait that runs out sets the error word and a CTA-wide abort
-// flag, every role leaves its loop, and the tensor memory is freed.
+// flag, every role leaves its loop, the producer waits (bounded) for the copies
+// it has in flight, the MMA issuer for its tensor-core operations, and the
+// tensor memory is freed.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -82,12 +84,14 @@ constexpr size_t kStageBytes = size_t(kTileM) * kMaxK0 * 2;                 // 1
 constexpr size_t kSmemStage = size_t(kPair) * kStageBytes;
 constexpr size_t kSmemRing = size_t(kSlots) * kSlotBytes;                   // weight chunks
 constexpr size_t kSmemBias = FNR_MLP_BIAS_SMEM ? size_t(kMaxBias) * 4 : 0;  // 16 KB biases (else read via L1)
-constexpr int kBars = 2 * kSlots + 5 * kPair;  // full, empty; acc_full, a_ready, enc_ready, enc_free, head_ready
+constexpr int kBars = 2 * kSlots + 5 * kPair + 1;  // full, empty; acc_full, a_ready, enc_ready, enc_free, head_ready;
+                                                   // drain
 constexpr size_t kSmemBars = (size_t(kBars) * 8 + 16 + 127) / 128 * 128;
 constexpr size_t kSmemBytes = kSmemA + kSmemStage + kSmemRing + kSmemBias + kSmemBars + 1024;  // + alignment slack
 static_assert(size_t(kTileM) * (kMaxHeadOut + 4) * 4 <= size_t(kTileM) * kMaxK * 2, "head staging fits an A tile");
 static_assert(kSmemBytes <= 232448, "shared memory per CTA");
 constexpr long long kWaitLimit = 1LL << 22;                                 // try_wait polls before giving up
+constexpr long long kDrainLimit = 1LL << 22;                                // polls for in-flight work at exit
 
 struct MlpLayerDev {
     const __nv_bfloat16 *w;  // chunk-major: chunk c = [Np][64] in the 128-byte swizzled K-major layout
@@ -119,6 +123,8 @@ struct MlpArgs {
     int n_out;        // outputs stored per point: 1 + 3D (mode 0), D (mode 1), out_stride (mode 2)
     int head_stride;  // floats per staged head row: round16(n_out) + 4
     int *err;
+    long long wait_limit;  // polls before a wait gives up (kWaitLimit unless a test armed a fault)
+    long long withhold;    // test fault: the producer withholds its chunk of this index (-1: none)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -143,15 +149,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: false when the limit runs out (the error word and the
+// Bounded wait: false when `limit` polls run out (the error word and the
 // CTA's abort flag are then set) or when another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag) {
-    for (long long it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag,
+                                          long long limit) {
+    for (long long it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 1023) == 1023 && *abort_flag) return false;
     }
     atomicExch(err, 1);
     *abort_flag = 1;
+    return false;
+}
+
+// Bounded wait at exit for work this CTA has in flight, abort or not; false
+// (and the error word set) if it does not complete within kDrainLimit polls.
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity, int *err) {
+    for (long long it = 0; it < kDrainLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicExch(err, 2);
     return false;
 }
 
@@ -333,6 +349,8 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
     auto enc_free = [&](int t) { return tile_bar(3, t); };
     // head_ready(t): every epilogue warp has staged its head outputs
     auto head_ready = [&](int t) { return tile_bar(4, t); };
+    // drain: the MMA issuer's last commit (every tensor-core operation of the CTA has completed)
+    const uint32_t drain_bar = bar0 + 8u * uint32_t(2 * kSlots + 5 * kPair);
     constexpr uint32_t kATileBytes = uint32_t(kTileM) * kMaxK * 2;
 
     if (FNR_MLP_BIAS_SMEM)
@@ -349,6 +367,7 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
             mbar_init(enc_free(t), 1);
             mbar_init(head_ready(t), kEpiWarps);
         }
+        mbar_init(drain_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -372,13 +391,15 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
     // a warp-wide bounded wait (lane 0 polls); false when it ran out or another role aborted
     auto warp_wait = [&](uint32_t bar, uint32_t parity) {
         int ok = 1;
-        if (lane == 0) ok = mbar_wait(bar, parity, A.err, &abort_flag) ? 1 : 0;
+        if (lane == 0) ok = mbar_wait(bar, parity, A.err, &abort_flag, A.wait_limit) ? 1 : 0;
         return __shfl_sync(0xffffffffu, ok, 0) != 0;
     };
 
     if (warp == kProducerWarp) {
         if (lane == 0) {
             long long it = 0;
+            long long issued[kSlots];  // per slot: the round of its last bulk copy (-1: none in flight)
+            for (int sl = 0; sl < kSlots; ++sl) issued[sl] = -1;
             for (long long r = 0; r < n_pairs && !abort_flag; ++r)
                 for (int li = 0; li < A.n_layers && !abort_flag; ++li)
                     for (int t = 0; t < kPair && !abort_flag; ++t) {
@@ -387,15 +408,21 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                         for (int c = 0; c < nc; ++c, ++it) {
                             const int slot = int(it % kSlots);
                             const long long round = it / kSlots;
-                            if (round > 0 &&
-                                !mbar_wait(empty_bar(slot), uint32_t((round - 1) & 1), A.err, &abort_flag))
+                            if (round > 0 && !mbar_wait(empty_bar(slot), uint32_t((round - 1) & 1), A.err,
+                                                        &abort_flag, A.wait_limit))
                                 break;
+                            if (it == A.withhold) continue;  // test fault: this chunk never arrives
                             const uint32_t bytes = uint32_t(Ly.N) * uint32_t(kChunkK) * 2u;
                             mbar_expect_tx(full_bar(slot), bytes);
                             const char *src = reinterpret_cast<const char *>(Ly.w) + size_t(c) * Ly.N * kChunkK * 2;
                             bulk_g2s(smem_u32(ring) + uint32_t(slot) * kSlotBytes, src, bytes, full_bar(slot));
+                            issued[slot] = round;
                         }
                     }
+            // Every copy issued has landed before the CTA's shared memory goes away
+            // (after an abort some may not have been waited for).
+            for (int sl = 0; sl < kSlots; ++sl)
+                if (issued[sl] >= 0) mbar_drain(full_bar(sl), uint32_t(issued[sl] & 1), A.err);
         }
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
@@ -404,8 +431,9 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                 for (int li = 0; li < A.n_layers && !abort_flag; ++li, ++uses)
                     for (int t = 0; t < kPair && !abort_flag; ++t) {
                         const MlpLayerDev &Ly = A.L[li];
-                        if (li == 0 && !mbar_wait(enc_ready(t), uint32_t(r & 1), A.err, &abort_flag)) break;
-                        if (!mbar_wait(a_ready(t), uint32_t(uses & 1), A.err, &abort_flag)) break;
+                        if (li == 0 && !mbar_wait(enc_ready(t), uint32_t(r & 1), A.err, &abort_flag, A.wait_limit))
+                            break;
+                        if (!mbar_wait(a_ready(t), uint32_t(uses & 1), A.err, &abort_flag, A.wait_limit)) break;
                         tc_fence_after();
                         const uint32_t idesc = instr_desc(kTileM, Ly.N);
                         const uint32_t a_base =
@@ -415,7 +443,9 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                         const int nc = n_chunks(Ly.K);
                         for (int c = 0; c < nc; ++c, ++it) {
                             const int slot = int(it % kSlots);
-                            if (!mbar_wait(full_bar(slot), uint32_t((it / kSlots) & 1), A.err, &abort_flag)) break;
+                            if (!mbar_wait(full_bar(slot), uint32_t((it / kSlots) & 1), A.err, &abort_flag,
+                                           A.wait_limit))
+                                break;
                             tc_fence_after();
 #pragma unroll
                             for (int s = 0; s < kChunkK / 16; ++s) {
@@ -431,6 +461,10 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                         if (li == 0) umma_commit(enc_free(t));  // the staging buffer may be refilled
                         umma_commit(acc_full(t));
                     }
+            // every tensor-core operation issued (and every commit before this one) has
+            // completed before the tensor memory is freed and the CTA leaves
+            umma_commit(drain_bar);
+            mbar_drain(drain_bar, 0u, A.err);
         }
     } else if (warp >= kEncWarp0 && warp < kEncWarp0 + kEncWarps) {
         // encoders: rows (warp - kEncWarp0) * 32 + lane + 32 kEncWarps i of each tile
@@ -664,9 +698,9 @@ fnr_status mlp_launch(const fnr_mlp *m, MlpArgs &A, int num_sms, cudaStream_t s)
         belems += size_t(round16(m->dims[i + 1]));
     }
     cudaError_t e;
-    if ((e = cudaMalloc(&wbuf.p, welems * 2)) != cudaSuccess) return cuda_fail(e, "MLP weights");
-    if ((e = cudaMalloc(&bbuf.p, belems * 4)) != cudaSuccess) return cuda_fail(e, "MLP biases");
-    if ((e = cudaMalloc(&ebuf.p, 4)) != cudaSuccess) return cuda_fail(e, "MLP error word");
+    if ((e = dev_malloc(&wbuf.p, welems * 2)) != cudaSuccess) return cuda_fail(e, "MLP weights");
+    if ((e = dev_malloc(&bbuf.p, belems * 4)) != cudaSuccess) return cuda_fail(e, "MLP biases");
+    if ((e = dev_malloc(&ebuf.p, 4)) != cudaSuccess) return cuda_fail(e, "MLP error word");
     if ((e = cudaMemsetAsync(ebuf.p, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "memset");
     size_t wo = 0, bo = 0;
     for (int i = 0; i < m->n_layers; ++i) {
@@ -688,6 +722,9 @@ fnr_status mlp_launch(const fnr_mlp *m, MlpArgs &A, int num_sms, cudaStream_t s)
     A.n_layers = m->n_layers;
     A.pe_freqs = m->pe_freqs;
     A.err = static_cast<int *>(ebuf.p);
+    A.wait_limit = kWaitLimit;
+    A.withhold = -1;
+    take_mlp_fault(&A.wait_limit, &A.withhold);
     A.n_out = A.mode == 0 ? 1 + 3 * A.D : (A.mode == 1 ? A.D : A.out_stride);
     A.head_stride = round16(A.n_out) + 4;
     if (A.n_out < 1 || A.n_out > kMaxHeadOut || A.n_out > A.L[m->n_layers - 1].N)
@@ -704,7 +741,8 @@ fnr_status mlp_launch(const fnr_mlp *m, MlpArgs &A, int num_sms, cudaStream_t s)
     if ((e = cudaMemcpyAsync(&herr, ebuf.p, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(e, "MLP sync");
-    if (herr) return fail(FNR_ERR_DEVICE, "MLP kernel: an mbarrier wait ran out");
+    if (herr == 1) return fail(FNR_ERR_DEVICE, "MLP kernel: an mbarrier wait ran out");
+    if (herr) return fail(FNR_ERR_DEVICE, "MLP kernel: work in flight did not drain at exit");
     return FNR_OK;
 }
 

@@ -460,7 +460,7 @@ static fnr_status server_start(fnr_context *ctx, const fnr_serve_config *cfg_in)
             (e = cudaEventCreateWithFlags(&s.done_ev, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaHostAlloc(reinterpret_cast<void **>(&s.h_table), sizeof(ServeTable), cudaHostAllocDefault)) !=
                 cudaSuccess ||
-            (e = cudaMalloc(&s.d_scratch, sizeof(ServeScratch))) != cudaSuccess ||
+            (e = dev_malloc(&s.d_scratch, sizeof(ServeScratch))) != cudaSuccess ||
             (e = cudaMemsetAsync(s.d_scratch, 0, sizeof(ServeScratch), s.stream)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s.stream)) != cudaSuccess ||
             (e = cudaHostAlloc(reinterpret_cast<void **>(&s.h_flags), sizeof(uint32_t) * kMaxBatch,

@@ -233,13 +233,13 @@ extern "C" fnr_status fnr_render_mlp(fnr_context *ctx, const fnr_mlp *pos_mlp, c
                     (unsigned long long)bytes);
     DevMem points, pos_out, dirs, dir_out, offset, count, total;
     st = FNR_OK;
-    if ((e = cudaMalloc(&points.p, size_t(max_pts) * 12)) != cudaSuccess ||
-        (e = cudaMalloc(&pos_out.p, size_t(max_pts) * (1 + 3 * D) * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&dirs.p, size_t(n_rays) * 12)) != cudaSuccess ||
-        (e = cudaMalloc(&dir_out.p, size_t(n_rays) * D * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&offset.p, size_t(n_rays) * 8)) != cudaSuccess ||
-        (e = cudaMalloc(&count.p, size_t(n_rays) * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&total.p, 8)) != cudaSuccess)
+    if ((e = dev_malloc(&points.p, size_t(max_pts) * 12)) != cudaSuccess ||
+        (e = dev_malloc(&pos_out.p, size_t(max_pts) * (1 + 3 * D) * 4)) != cudaSuccess ||
+        (e = dev_malloc(&dirs.p, size_t(n_rays) * 12)) != cudaSuccess ||
+        (e = dev_malloc(&dir_out.p, size_t(n_rays) * D * 4)) != cudaSuccess ||
+        (e = dev_malloc(&offset.p, size_t(n_rays) * 8)) != cudaSuccess ||
+        (e = dev_malloc(&count.p, size_t(n_rays) * 4)) != cudaSuccess ||
+        (e = dev_malloc(&total.p, 8)) != cudaSuccess)
         st = cuda_fail(e, "uncached render temporaries");
     unsigned long long n_pts = 0;
     if (st == FNR_OK) {

@@ -117,3 +117,14 @@ def test_binding_constants_match_header(fnr):
     for n in ("FNR_RENDER_SKIP_EMPTY", "FNR_RENDER_DIR_BILINEAR", "FNR_RENDER_VOXELS", "FNR_ERR_IO",
               "FNR_LAYOUT_BRICKS"):
         assert n in binding, n
+
+
+def test_testing_hooks_validate_arguments(fnr):
+    """The failure-injection hooks (fnr_testing.h) check their arguments and arm / disarm without touching
+    the device."""
+    L = fnr.lib()
+    assert L.fnr_testing_fail_allocations(-1, 1) == fnr.FNR_ERR_INVALID_ARG
+    assert L.fnr_testing_fail_allocations(0, -1) == fnr.FNR_ERR_INVALID_ARG
+    assert L.fnr_testing_mlp_fault(0, 3) == fnr.FNR_ERR_INVALID_ARG
+    assert L.fnr_testing_fail_allocations(2, 1) == fnr.FNR_OK
+    assert L.fnr_testing_fail_allocations(0, 0) == fnr.FNR_OK  # disarmed

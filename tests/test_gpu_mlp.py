@@ -2,14 +2,21 @@
 
 Checked against the FP64 oracle's MLP evaluated at the same grid samples:
 (i) with the same bf16 weights and bf16 rounding of the network input and of
-every hidden activation (as the tensor-core chain stores them): per output
-channel relative L2 error <= 5e-3 and max |error| <= 8e-2 * rms(channel). The
-chain rounds fp32 accumulators to bf16 where the oracle rounds FP64 ones, so an
-activation near a bf16 rounding boundary can land one bf16 ulp (2^-8) apart and
-carry that through the later layers: rare, hence the max bound well above the
-L2 one (first measured run: max 3.8e-2 * rms). (ii) against pure FP64
-activations: relative L2 <= 5e-2. A single linear layer (no hidden rounding) is
-checked tightly (FP32 accumulation only), which pins the operand layouts."""
+every hidden activation (as the tensor-core chain stores them), per output
+channel: relative L2 error <= 2.5e-3, at least 99% of the values within
+1e-2 * rms(channel), and max |error| <= 0.13 * rms(channel). The chain rounds
+fp32 accumulators to bf16 where the oracle rounds FP64 ones. The fp32 sum of
+256 exact bf16 products differs from the FP64 one by ~1e-6 relative, so about
+one activation in 2,000 lies close enough to a bf16 rounding boundary to land
+one bf16 ulp (2^-8 relative) apart; F_pos has 2,048 hidden activations per
+point, so most points carry a flip or two through the later layers. That sets
+the bulk (measured at 1,048,576 points: relative L2 1.3e-3, 99.65% of values
+within 1e-2 rms in the worst channel) and the rare large outliers (measured
+max 8.7e-2 rms); the bounds above were frozen from that run with headroom.
+(ii) against pure FP64 activations: relative L2 <= 5e-2. A single linear layer
+(no hidden rounding) is checked tightly (FP32 accumulation only), which pins
+the operand layouts. The full-size build (F_pos over 512^3, F_dir over 512^2)
+is checked on 1,048,576 random grid points and 65,536 random direction bins."""
 
 import numpy as np
 import pytest
@@ -69,13 +76,21 @@ def build(fnr, ctx, k, l, D, pos, dirn, prec=0, dprec=0):
     return fnr.fnr_build_cache_mlp(ctx, desc, to_device(pos), to_device(dirn))
 
 
-def check_channels(got, ref, l2_rel=5e-3, max_rel=8e-2):
+def check_channels(got, ref, l2_rel=2.5e-3, max_rel=0.13, bulk_rel=1e-2, bulk_frac=0.99):
     rms = np.sqrt(np.mean(ref ** 2, axis=0)) + 1e-12
-    l2 = np.sqrt(np.mean((got - ref) ** 2, axis=0)) / rms
-    mx = np.max(np.abs(got - ref), axis=0) / rms
-    print(f"per-channel relative L2 max {l2.max():.2e}, max |err|/rms {mx.max():.2e}")
+    err = np.abs(got - ref) / rms
+    l2 = np.sqrt(np.mean(err ** 2, axis=0))
+    mx = np.max(err, axis=0)
+    within = np.mean(err <= bulk_rel, axis=0)
+    tail = {t: float(np.mean(err <= t, axis=0).min()) for t in (2e-2, 3e-2, 5e-2)}
+    print(f"per-channel relative L2 max {l2.max():.2e}, max |err|/rms {mx.max():.2e}, "
+          f"fraction within {bulk_rel:g} rms min {within.min():.6f}, within 2e-2/3e-2/5e-2 "
+          f"{tail[2e-2]:.6f}/{tail[3e-2]:.6f}/{tail[5e-2]:.6f} ({got.shape[0]} points)")
     assert np.all(l2 <= l2_rel), l2.max()
+    assert np.all(within >= bulk_frac), within.min()
     assert np.all(mx <= max_rel), mx.max()
+    return {"rel_l2_max": float(l2.max()), "max_abs_over_rms": float(mx.max()),
+            "frac_within_bulk_min": float(within.min())}
 
 
 def test_single_linear_layer(fnr):
@@ -112,19 +127,19 @@ def test_full_architecture_small_grid(fnr, prec):
         ref_b = oracle.mlp_eval(as_fp64(pos), xyz, 10, True)
         got = np.concatenate([sig[:, None], uvw], axis=1)
         ref = np.concatenate([np.maximum(ref_b[:, :1], 0), ref_b[:, 1:]], axis=1)
-        check_channels(got, ref, 5e-3 if prec == 0 else 6e-3)
+        check_channels(got, ref, 2.5e-3 if prec == 0 else 3e-3)
         ref64 = oracle.mlp_eval(as_fp64(pos), xyz, 10, False)
         rel = np.linalg.norm(uvw - ref64[:, 1:]) / np.linalg.norm(ref64[:, 1:])
         assert rel < 5e-2, rel
         dirs = oracle.bin_directions(l, np.arange(l * l))
-        check_channels(beta, oracle.mlp_eval(as_fp64(dirn), dirs, 4, True), 5e-3 if prec == 0 else 6e-3)
+        check_channels(beta, oracle.mlp_eval(as_fp64(dirn), dirs, 4, True), 2.5e-3 if prec == 0 else 3e-3)
     finally:
         fnr.fnr_context_destroy(ctx)
 
 
 def test_cache_build_config_sampled(fnr):
-    """F_pos over 512^3 and F_dir over 512^2 (He-uniform, seed 0), checked on 32768 random grid points
-    (seed 1) and 4096 random direction bins; then a render of the built cache matches the oracle."""
+    """F_pos over 512^3 and F_dir over 512^2 (He-uniform, seeds 0 and 100), checked on 1,048,576 random grid
+    points (seed 1) and 65,536 random direction bins against the FP64 oracle MLP."""
     import torch
     k, l, D = 512, 512, 8
     pos = scenegen.mlp_weights(0, scenegen.FPOS_DIMS_D8)
@@ -134,7 +149,7 @@ def test_cache_build_config_sampled(fnr):
         cache = build(fnr, ctx, k, l, D, pos, dirn)
         torch.cuda.synchronize()
         rng = np.random.default_rng(1)
-        cells = rng.integers(0, k ** 3, 32768)
+        cells = rng.integers(0, k ** 3, 1 << 20)
         lay = fnr.fnr_cache_get_layout(cache)
         sig_all = device_bytes(lay.sigma_dev, k ** 3 * 4).view(np.float32)
         ref = oracle.mlp_eval(as_fp64(pos), oracle.cell_centres(k, cells), 10, True)
@@ -144,7 +159,7 @@ def test_cache_build_config_sampled(fnr):
         uvw = rec[torch.from_numpy(cells).cuda()].cpu().numpy().astype(np.float64)[:, :3 * D]
         got = np.concatenate([sig_all[cells].astype(np.float64)[:, None], uvw], axis=1)
         check_channels(got, np.concatenate([np.maximum(ref[:, :1], 0), ref[:, 1:]], axis=1))
-        bins = rng.integers(0, l * l, 4096)
+        bins = rng.integers(0, l * l, 65536)
         beta_all = device_bytes(lay.beta_dev, l * l * D * 4).view(np.float32).reshape(l * l, D)
         check_channels(beta_all[bins].astype(np.float64),
                        oracle.mlp_eval(as_fp64(dirn), oracle.bin_directions(l, bins), 4, True))
