@@ -230,12 +230,22 @@ typedef struct {
     const int32_t *page_table_dev; /* BRICKS: [nb^3] brick slot, -1 for an empty brick (same brick
                                       index as the occupancy bits); NULL for DENSE */
     uint64_t n_bricks;         /* BRICKS: bricks stored */
+    const uint8_t *brick_distance_dev; /* distance field for passing over empty space: the grid is
+                                      cut into jump bricks of J = distance_brick cells a side (J =
+                                      B 2^m, the smallest with nj = ceil(k / J) <= 32); a jump brick
+                                      is occupied iff one of its occupancy bricks is; entry
+                                      (jz nj + jy) nj + jx holds the Chebyshev distance, in jump
+                                      bricks, to the nearest occupied jump brick, capped at 16 (0 when
+                                      occupied); every jump brick within distance - 1 of it is empty.
+                                      Used by FNR_RENDER_SKIP_EMPTY renders. [nj^3] bytes */
+    int32_t distance_brick;    /* J */
+    int32_t reserved2;
 } fnr_cache_layout;
 FNR_API fnr_status fnr_cache_get_layout(const fnr_cache *cache, fnr_cache_layout *out);
 
 /* Persist a built cache (no counterpart in the paper, which keeps its caches
  * in memory): the file holds a header -- the 8 bytes "FNRCACHE", a uint32
- * format version (1), the uint32 header size, the fnr_cache_desc, the uint64
+ * format version (2), the uint32 header size, the fnr_cache_desc, the uint64
  * device footprint and the uint64 brick count (FNR_LAYOUT_BRICKS; else 0) --
  * followed by the cache's device allocation byte
  * for byte (every section of fnr_cache_layout, whose offsets follow from the

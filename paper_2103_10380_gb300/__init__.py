@@ -75,7 +75,8 @@ class fnr_cache_layout(ctypes.Structure):
                 ("phi_key_dev", ctypes.c_void_p), ("occupancy_dev", ctypes.c_void_p),
                 ("record_stride", ctypes.c_int32), ("occupancy_brick", ctypes.c_int32), ("footprint", ctypes.c_uint64),
                 ("layout", ctypes.c_int32), ("reserved1", ctypes.c_int32), ("page_table_dev", ctypes.c_void_p),
-                ("n_bricks", ctypes.c_uint64)]
+                ("n_bricks", ctypes.c_uint64), ("brick_distance_dev", ctypes.c_void_p),
+                ("distance_brick", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class fnr_camera(ctypes.Structure):

@@ -45,7 +45,7 @@ int rec_stride_bytes(int prec, int D) {
 static uint64_t align256(uint64_t v) { return (v + 255u) & ~uint64_t(255u); }
 
 struct Layout {
-    uint64_t off_sigma, off_uvw, off_beta, off_ct, off_qp, off_scales, off_occ, off_page, off_rank, total;
+    uint64_t off_sigma, off_uvw, off_beta, off_ct, off_qp, off_scales, off_occ, off_dist, off_page, off_rank, total;
     int rec_stride;
 };
 
@@ -59,6 +59,14 @@ int occupancy_shift(const fnr_cache_desc *d) {
     }
     int sh = 1;
     while ((d->k + (1 << sh) - 1) >> sh > 64) ++sh;
+    return sh;
+}
+
+// Jump-brick side of the distance field: the smallest power-of-two multiple of
+// the occupancy brick with ceil(k / J) <= kDistMaxDim.
+int distance_shift(const fnr_cache_desc *d) {
+    int sh = occupancy_shift(d);
+    while ((d->k + (1 << sh) - 1) >> sh > kDistMaxDim) ++sh;
     return sh;
 }
 
@@ -105,6 +113,9 @@ static Layout layout_of(const fnr_cache_desc *d, int64_t n_bricks = -1) {
     off = align256(off + uint64_t(1 + 3 * d->D) * 4);
     L.off_occ = off;
     off = align256(off + occupancy_words(d) * 4);
+    L.off_dist = off;
+    const uint64_t nj = uint64_t((d->k + (1 << distance_shift(d)) - 1) >> distance_shift(d));
+    off = align256(off + nj * nj * nj);
     L.off_page = off;
     if (bricks) off = align256(off + nb * nb * nb * 4);
     L.off_rank = off;
@@ -240,11 +251,14 @@ static void fill_view(fnr_cache *c, const Layout &L) {
     v.qp = reinterpret_cast<const float *>(base + L.off_qp);
     v.scales = reinterpret_cast<const float *>(base + L.off_scales);
     v.occ = reinterpret_cast<const uint32_t *>(base + L.off_occ);
+    v.dist = reinterpret_cast<const uint8_t *>(base + L.off_dist);
     v.layout = c->n_bricks > 0 || d.layout == FNR_LAYOUT_BRICKS ? FNR_LAYOUT_BRICKS : FNR_LAYOUT_DENSE;
     v.page = v.layout == FNR_LAYOUT_BRICKS ? reinterpret_cast<const int32_t *>(base + L.off_page) : nullptr;
     v.rank = v.layout == FNR_LAYOUT_BRICKS ? reinterpret_cast<const uint32_t *>(base + L.off_rank) : nullptr;
     v.occ_shift = occupancy_shift(&d);
     v.occ_dim = (d.k + (1 << v.occ_shift) - 1) >> v.occ_shift;
+    v.dist_shift = distance_shift(&d);
+    v.dist_dim = (d.k + (1 << v.dist_shift) - 1) >> v.dist_shift;
     for (int a = 0; a < 3; ++a) {
         v.bmin[a] = d.bmin[a];
         v.scale[a] = static_cast<float>(static_cast<double>(d.k) /
@@ -448,7 +462,8 @@ static fnr_status make_bricks(fnr_context *ctx, const fnr_cache *dense, const fn
          (e = cudaMemcpyAsync(base + L.off_beta, dbase + LD.off_beta, L.off_page - L.off_beta,
                               cudaMemcpyDeviceToDevice, s)) != cudaSuccess))
         st = cuda_fail(e, "brick cache tables");
-    // (beta, the bin tables, the scales and the occupancy bits keep their relative offsets)
+    // (beta, the bin tables, the scales, the occupancy bits and the brick distances keep their
+    // relative offsets)
     if (st == FNR_OK && n_bricks > 0 &&
         (e = launch_gather_bricks(dv.sigma, dv.uvw, base + L.off_sigma, base + L.off_uvw,
                                   static_cast<const int32_t *>(slots.p), n_bricks, desc->k, dv.occ_shift,
@@ -548,6 +563,9 @@ fnr_status fnr_build_cache(fnr_context *ctx, const fnr_cache_desc *desc, const f
         fill_view(c, L);
         if ((e = cudaMemsetAsync(base + L.off_occ, 0, occupancy_words(desc) * 4, s)) != cudaSuccess ||
             (e = launch_occupancy(c->view, reinterpret_cast<uint32_t *>(base + L.off_occ), s)) != cudaSuccess ||
+            (e = launch_brick_distance(reinterpret_cast<const uint32_t *>(base + L.off_occ), c->view.occ_dim,
+                                       c->view.occ_shift, reinterpret_cast<uint8_t *>(base + L.off_dist),
+                                       c->view.dist_dim, c->view.dist_shift, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
             st = cuda_fail(e, "occupancy bits");
     }
@@ -585,7 +603,7 @@ fnr_status fnr_cache_free(fnr_context *ctx, fnr_cache *c) {
 // ---------------------------------------------------------------- save / load
 namespace {
 constexpr char kFileMagic[8] = {'F', 'N', 'R', 'C', 'A', 'C', 'H', 'E'};
-constexpr uint32_t kFileVersion = 1;
+constexpr uint32_t kFileVersion = 2;  // 2: the brick distance field follows the occupancy bits
 struct FileHeader {
     char magic[8];
     uint32_t version;
@@ -724,6 +742,9 @@ fnr_status fnr_cache_get_layout(const fnr_cache *c, fnr_cache_layout *out) {
     out->layout = v.layout;
     out->reserved1 = 0;
     out->page_table_dev = v.page;
+    out->brick_distance_dev = v.dist;
+    out->distance_brick = 1 << v.dist_shift;
+    out->reserved2 = 0;
     out->n_bricks = c->n_bricks;
     out->footprint = c->footprint;
     return FNR_OK;

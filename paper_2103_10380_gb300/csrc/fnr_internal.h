@@ -24,8 +24,12 @@ struct CacheView {
     const uint32_t *occ;  // brick occupancy bits, brick (bz * occ_dim + by) * occ_dim + bx
     const int32_t *page;  // FNR_LAYOUT_BRICKS: brick -> pool slot (-1 empty); sigma / uvw are the pools
     const uint32_t *rank; // FNR_LAYOUT_BRICKS: set occupancy bits in the words before each word
+    const uint8_t *dist;  // per jump brick: Chebyshev distance (jump bricks) to the nearest occupied one,
+                          // capped at kDistCap + 1
     int32_t occ_shift;    // log2 of the brick side in cells
     int32_t occ_dim;      // bricks per axis, ceil(k / 2^occ_shift)
+    int32_t dist_shift;   // log2 of the jump-brick side in cells (>= occ_shift)
+    int32_t dist_dim;     // jump bricks per axis, ceil(k / 2^dist_shift) <= kDistMaxDim
     int32_t layout;       // FNR_LAYOUT_*
     float bmin[3];
     float scale[3];       // binary32(k / (bmax - bmin)) per axis
@@ -123,6 +127,14 @@ cudaError_t launch_absmax(const float *sigma, const float *uvw, int64_t n_cells,
 cudaError_t launch_occupancy(const CacheView &v, uint32_t *words, cudaStream_t s);
 int occupancy_shift(const fnr_cache_desc *d);
 uint64_t occupancy_words(const fnr_cache_desc *d);
+// Distance field for passing over empty space: the Chebyshev distance transform of the occupancy
+// at jump-brick resolution (2^dist_shift cells, at most kDistMaxDim jump bricks per axis, so the
+// field is at most 32 KB and stays in L1); distances above kDistCap read kDistCap + 1.
+constexpr int kDistCap = 15;
+constexpr int kDistMaxDim = 32;
+int distance_shift(const fnr_cache_desc *d);
+cudaError_t launch_brick_distance(const uint32_t *words, int nb, int occ_shift, uint8_t *dist, int nj,
+                                  int dist_shift, cudaStream_t s);
 cudaError_t launch_scales_from_absmax(const unsigned *amax_bits, float *scales, int n, cudaStream_t s);
 
 struct Server;

@@ -219,6 +219,7 @@ __device__ __noinline__ void stage_beta_bilinear(const CacheView &c, float dx, f
 template <int PREC, int D>
 struct RaySetup {
     float e[3], f[3];
+    float inv_emax;    // approximate 1 / max_a |e_a| (skipping only)
     int i_lo, i_hi;
     int in_lo, in_hi;  // samples certainly inside the box (the exact test is then redundant)
     int dcell;
@@ -275,6 +276,7 @@ struct RaySetup {
             }
         }
         i_lo = min(i_lo, r.N);
+        inv_emax = __frcp_rn(fmaxf(fabsf(e[0]), fmaxf(fabsf(e[1]), fabsf(e[2]))));
         // The same bound narrowed by one cell on every face and two samples at
         // each end: samples in [in_lo, in_hi) have 1 <= g_a <= k - 1 on every axis
         // with room to spare for the rounding of g and of these bounds, so the
@@ -373,6 +375,50 @@ struct RaySetup {
         const int iz = __float2int_rd(__fmaf_rn(fi, e[2], f[2]));
         brick = ((iz >> c.occ_shift) * c.occ_dim + (iy >> c.occ_shift)) * c.occ_dim + (ix >> c.occ_shift);
         return (iz * c.k + iy) * c.k + ix;
+    }
+
+    // Empty-space skipping over runs of samples (FNR_RENDER_SKIP_EMPTY), one
+    // step: the first sample >= s that this lane must still test -- s itself
+    // unless s lies in an empty jump brick, INT_MAX when no sample is left in
+    // [s, i_hi). A sample in jump brick b (J cells a side) at distance d >= 1
+    // from every occupied one lies in the cube of jump bricks b - (d - 1) ..
+    // b + (d - 1), which holds no density. Along axis a the sample's binary32
+    // coordinate g_a is r_a = ((b_a + 1) J - g_a or g_a - b_a J, by the sign
+    // of e_a) from the face of its brick ahead of it, so (d - 1) J + r_a from the
+    // cube's face (an axis with e_a = 0 never reaches it), and no sample moves
+    // more than emax = max_a |e_a| cells along any axis: after n samples with n emax <= (d - 1) J + min_a r_a - 1/100 the
+    // ray is still inside the cube (1/100 cell covers the roundings, each below
+    // 2^-12 cell for k < 2048), and by monotonicity of the per-axis binary32
+    // coordinate in the sample index so is every sample in between. Those
+    // samples lie in empty bricks: the per-sample test would not look them up.
+    __device__ __forceinline__ int skip_empty_step(const CacheView &c, int s) const {
+        if (s >= i_hi) return 0x7fffffff;
+        const float fs = __fadd_rn(static_cast<float>(s), 0.5f);
+        float g[3];
+        int ci[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            g[a] = __fmaf_rn(fs, e[a], f[a]);
+            ci[a] = __float2int_rd(g[a]);
+        }
+        const unsigned int ku = static_cast<unsigned int>(c.k);
+        if (!(static_cast<unsigned int>(ci[0]) < ku && static_cast<unsigned int>(ci[1]) < ku &&
+              static_cast<unsigned int>(ci[2]) < ku))
+            return s;
+        const int sh = c.dist_shift;
+        const int d = __ldg(c.dist + ((ci[2] >> sh) * c.dist_dim + (ci[1] >> sh)) * c.dist_dim + (ci[0] >> sh));
+        if (d == 0) return s;
+        float reach = 3.0e38f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int face = ((ci[a] >> sh) + (e[a] > 0.0f ? 1 : 0)) << sh;
+            const float ra = e[a] > 0.0f ? static_cast<float>(face) - g[a] : g[a] - static_cast<float>(face);
+            if (e[a] != 0.0f) reach = fminf(reach, ra);  // no motion along a: no limit
+        }
+        reach += static_cast<float>((d - 1) << sh) - 0.01f;
+        const int n = __float2int_rd(fminf(reach * inv_emax, 1.0e9f));
+        if (n <= 0) return s;
+        return n < i_hi - s ? s + n + 1 : 0x7fffffff;
     }
 
     // a7: Eq. 5 and the activation for one record.
@@ -514,9 +560,25 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
 
     // empty-group test by the maximum density (measured faster for binary32 densities only)
     constexpr bool kMaxTest = PREC == FNR_PREC_FP32;
+    // skipping passes over runs of samples in empty space (not when every sample's cell is written)
+    const bool jump = SKIP && F.cells == nullptr;
     int qn = 0;
     for (int i0 = lo_w; i0 < hi_w; i0 += kUnroll) {
         if (!__any_sync(FULL, !done)) break;
+        if (SKIP && jump) {
+            // The warp moves on, a step at a time, to the first sample some marching lane must
+            // still test; each step is one cube of empty jump bricks for every lane, and the
+            // steps stop as soon as one lane cannot advance.
+#pragma unroll 1
+            for (int st = 0; st < 4; ++st) {
+                const int t = done ? 0x7fffffff : R.skip_empty_step(c, max(i0, R.i_lo));
+                const int m = __reduce_min_sync(FULL, t);
+                if (m <= i0) break;
+                i0 = m;
+                if (i0 >= hi_w) break;
+            }
+            if (i0 >= hi_w) break;
+        }
         // samples of this group the lane visits: [i_lo, i_hi) before termination
         const int vlo = min(max(R.i_lo - i0, 0), kUnroll), vhi = min(max(R.i_hi - i0, 0), kUnroll);
         const unsigned vis = done ? 0u : (((1u << vhi) - 1u) & ~((1u << vlo) - 1u));

@@ -118,6 +118,55 @@ __global__ void occupancy_kernel(const CacheView v, uint32_t *__restrict__ words
     }
 }
 
+// Distance field for passing over empty space: the Chebyshev (L-infinity)
+// distance, in jump bricks (2^m occupancy bricks a side), from each jump brick
+// to the nearest occupied one. Initial pass: 0 for jump bricks holding an
+// occupied brick, unset (255) for the others; pass r = 1 .. kDistCap gives r
+// to every unset jump brick with a neighbour (3 x 3 x 3) at r - 1 -- one at
+// distance r always has one, and one still unset after pass r - 1 is at
+// distance >= r; updating in place is safe since a pass reads only r - 1 and
+// writes r; the last pass gives kDistCap + 1 to those still unset.
+__global__ void dist_init_kernel(const uint32_t *__restrict__ words, int nb, int m, uint8_t *__restrict__ dist,
+                                 int nj) {
+    const int64_t nj3 = static_cast<int64_t>(nj) * nj * nj;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < nj3; j += stride) {
+        const int jx = static_cast<int>(j % nj), jy = static_cast<int>((j / nj) % nj), jz = static_cast<int>(j / nj / nj);
+        bool occ = false;
+        for (int z = jz << m; z < min((jz + 1) << m, nb) && !occ; ++z)
+            for (int y = jy << m; y < min((jy + 1) << m, nb) && !occ; ++y)
+                for (int x = jx << m; x < min((jx + 1) << m, nb) && !occ; ++x) {
+                    const int64_t b = (static_cast<int64_t>(z) * nb + y) * nb + x;
+                    occ = (words[b >> 5] >> (b & 31)) & 1u;
+                }
+        dist[j] = occ ? uint8_t(0) : uint8_t(255);
+    }
+}
+
+__global__ void dist_pass_kernel(uint8_t *__restrict__ dist, int nb, int r) {
+    const int64_t nb3 = static_cast<int64_t>(nb) * nb * nb;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; b < nb3; b += stride) {
+        if (dist[b] != 255) continue;
+        const int x = static_cast<int>(b % nb), y = static_cast<int>((b / nb) % nb), z = static_cast<int>(b / nb / nb);
+        bool near = false;
+        for (int dz = -1; dz <= 1 && !near; ++dz)
+            for (int dy = -1; dy <= 1 && !near; ++dy)
+                for (int dx = -1; dx <= 1 && !near; ++dx) {
+                    const int xx = x + dx, yy = y + dy, zz = z + dz;
+                    if (xx < 0 || yy < 0 || zz < 0 || xx >= nb || yy >= nb || zz >= nb) continue;
+                    near = dist[(static_cast<int64_t>(zz) * nb + yy) * nb + xx] == r - 1;
+                }
+        if (near) dist[b] = static_cast<uint8_t>(r);
+    }
+}
+
+__global__ void dist_cap_kernel(uint8_t *__restrict__ dist, int64_t nb3) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; b < nb3; b += stride)
+        if (dist[b] == 255) dist[b] = static_cast<uint8_t>(kDistCap + 1);
+}
+
 // One pool element per thread: cell (x, y, z) of brick slot_brick[slot] at
 // pool index slot B^3 + (lz B + ly) B + lx; cells past the grid edge are 0.
 __global__ void gather_bricks_kernel(const char *__restrict__ sigma, const char *__restrict__ uvw,
@@ -160,6 +209,17 @@ cudaError_t launch_occupancy(const CacheView &v, uint32_t *words, cudaStream_t s
     if (v.pos_prec == FNR_PREC_FP16) occupancy_kernel<FNR_PREC_FP16><<<blocks, 256, 0, s>>>(v, words);
     else if (v.pos_prec == FNR_PREC_FP8_E4M3) occupancy_kernel<FNR_PREC_FP8_E4M3><<<blocks, 256, 0, s>>>(v, words);
     else occupancy_kernel<FNR_PREC_FP32><<<blocks, 256, 0, s>>>(v, words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_distance(const uint32_t *words, int nb, int occ_shift, uint8_t *dist, int nj,
+                                  int dist_shift, cudaStream_t s) {
+    const int64_t nj3 = static_cast<int64_t>(nj) * nj * nj;
+    if (nj3 <= 0) return cudaSuccess;
+    const unsigned blocks = grid_for(nj3, 256);
+    dist_init_kernel<<<blocks, 256, 0, s>>>(words, nb, dist_shift - occ_shift, dist, nj);
+    for (int r = 1; r <= kDistCap; ++r) dist_pass_kernel<<<blocks, 256, 0, s>>>(dist, nj, r);
+    dist_cap_kernel<<<blocks, 256, 0, s>>>(dist, nj3);
     return cudaGetLastError();
 }
 

@@ -1,11 +1,15 @@
 """Empty-space skipping (FNR_RENDER_SKIP_EMPTY) through the C ABI.
 
 The cache's brick occupancy bits must equal the oracle's (bit-exact, from the
-stored densities of each precision); a skip render must give the plain
-render's image and counters bit for bit except the lookup count, which must
-equal the oracle's skip-mode count (in-box samples in occupied bricks, up to
-termination); colours within 1e-5 of the FP64 oracle. Served skip requests,
-mixed with plain ones, must equal fnr_render's skip output bit for bit."""
+stored densities of each precision), and its brick distance field the
+brute-force Chebyshev distance to the nearest occupied brick; a skip render
+must give the plain render's image and counters bit for bit except the lookup
+count, which must equal the oracle's skip-mode count (in-box samples in
+occupied bricks, up to termination); colours within 1e-5 of the FP64 oracle.
+Without per-sample cell output the march passes over runs of samples the
+distance field proves empty: those renders must equal the ones with cell
+output bit for bit. Served skip requests, mixed with plain ones, must equal
+fnr_render's skip output bit for bit."""
 
 import numpy as np
 import pytest
@@ -72,6 +76,57 @@ def occupancy_from_device(lay, k):
     return B, bits[:nb ** 3]
 
 
+def chebyshev_distance(occ, nb, cap=15):
+    """Brute force: per brick, min over occupied bricks of the L-infinity index distance, capped at cap + 1."""
+    idx = np.stack(np.meshgrid(np.arange(nb), np.arange(nb), np.arange(nb), indexing="ij"), -1).reshape(-1, 3)
+    idx = idx[:, ::-1]  # brick (bz nb + by) nb + bx -> (bx, by, bz)
+    occupied = idx[occ.astype(bool)]
+    out = np.full(nb ** 3, cap + 1, np.int64)
+    for lo in range(0, occupied.shape[0], 256):
+        o = occupied[lo:lo + 256]
+        d = np.abs(idx[:, None, :] - o[None, :, :]).max(-1).min(1)
+        out = np.minimum(out, d)
+    return np.minimum(out, cap + 1)
+
+
+def axis_ray_camera():
+    """Identity rotation (looking down -z) from (0.013, -0.021, 3.7); pixel (16, 16) of 33 x 33 has
+    d = (0, 0, -1) exactly, so its x and y sample coordinates are constant."""
+    return dict(c2w=np.array([1, 0, 0, 0.013, 0, 1, 0, -0.021, 0, 0, 1, 3.7], np.float32), fx=np.float32(30.0),
+                fy=np.float32(30.0), cx=np.float32(16.5), cy=np.float32(16.5), W=33, H=33)
+
+
+@pytest.mark.parametrize("brick", [0, 1, 4, 8])
+def test_brick_distance_field(fnr, ctx, tiny_workload, tiny_arrays, brick):
+    """The distance field: jump bricks J = B 2^m (smallest with ceil(k / J) <= 32), occupied iff one of their
+    occupancy bricks is, each holding the capped Chebyshev distance to the nearest occupied jump brick."""
+    w = tiny_workload
+    sig, uvw, beta = tiny_arrays
+    sparse = sig.copy().reshape(w.k, w.k, w.k)
+    sparse[:, :, : w.k // 2] = 0  # a large empty half-space: distances up to the cap
+    for s_ in (sig, sparse):
+        cache = fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, occupancy_brick=brick), s_.reshape(-1),
+                                    uvw.reshape(-1), beta.reshape(-1))
+        try:
+            lay = fnr.fnr_cache_get_layout(cache)
+            B, bits = occupancy_from_device(lay, w.k)
+            nb = (w.k + B - 1) // B
+            J = lay.distance_brick
+            m = J // B
+            assert J % B == 0 and m & (m - 1) == 0 and -(-w.k // J) <= 32 and (J == B or -(-w.k // (J // 2)) > 32)
+            nj = -(-w.k // J)
+            occ = bits.reshape(nb, nb, nb)
+            coarse = np.zeros((nj, nj, nj), bool)
+            for z in range(nb):
+                for y in range(nb):
+                    coarse[z // m, y // m] |= np.add.reduceat(occ[z, y], np.arange(0, nb, m)) > 0
+            dist = device_bytes(lay.brick_distance_dev, nj ** 3).astype(np.int64)
+            assert np.array_equal(dist, chebyshev_distance(coarse.reshape(-1), nj))
+            assert np.array_equal(dist == 0, coarse.reshape(-1))
+        finally:
+            fnr.fnr_cache_free(ctx, cache)
+
+
 @pytest.mark.parametrize("prec,dprec", [(0, 0), (1, 1), (2, 1)])
 @pytest.mark.parametrize("brick", [0, 1, 4, 16])
 def test_tiny_skip_parity(fnr, ctx, tiny_workload, tiny_arrays, prec, dprec, brick):
@@ -87,7 +142,9 @@ def test_tiny_skip_parity(fnr, ctx, tiny_workload, tiny_arrays, prec, dprec, bri
         assert np.array_equal(bits, oc.occ)
         cases = [(w.cameras()[0], dict()), (w.cameras()[0], dict(t_thr=0.0)),
                  (scenegen.look_at_camera((0.1, 0.2, 0.3), 30, 20), dict(t_near=0.0, t_far=3.0)),
-                 (scenegen.cameras(41, 1, 37, 29)[0], dict(t_thr=1e-3))]
+                 (scenegen.cameras(41, 1, 37, 29)[0], dict(t_thr=1e-3)),
+                 (axis_ray_camera(), dict(t_near=0.5, t_far=7.0)),
+                 (scenegen.cameras(43, 1, 24, 24, radius=9.0)[0], dict(t_near=5.0, t_far=13.0))]
         for cam, kw in cases:
             p = fnr.make_params(w.n_samples, **kw)
             ps = fnr.make_params(w.n_samples, skip_empty=True, **kw)
@@ -96,6 +153,8 @@ def test_tiny_skip_parity(fnr, ctx, tiny_workload, tiny_arrays, prec, dprec, bri
             assert np.array_equal(got[0], plain[0])  # image bit for bit
             assert np.array_equal(got[1][..., [0, 2, 3]], plain[1][..., [0, 2, 3]])
             assert np.array_equal(got[2], plain[2])
+            fast = render(fnr, ctx, cache, cam, ps, with_cells=False)  # passes over empty runs
+            assert np.array_equal(fast[0], got[0]) and np.array_equal(fast[1], got[1])
             ref = oracle.render_image(oc, cam, oparams(ps), want_cells=True)
             assert np.array_equal(got[1], ref[1]), f"counters differ at {np.argwhere(got[1] != ref[1])[:5]}"
             assert np.max(np.abs(got[0].astype(np.float64) - ref[0])) <= TOL
@@ -197,6 +256,9 @@ def test_component_counts_skip_bricks_bilinear(fnr, ctx, D):
                 got = render(fnr, ctx, dense, cam, p)
                 got_b = render(fnr, ctx, bricks, cam, p)
                 assert np.array_equal(got_b[0], got[0]) and np.array_equal(got_b[1], got[1])
+                for c_ in (dense, bricks):  # passing over empty runs
+                    fast = render(fnr, ctx, c_, cam, p, with_cells=False)
+                    assert np.array_equal(fast[0], got[0]) and np.array_equal(fast[1], got[1])
                 ref = oracle.render_image(oc, cam, oparams(p), want_cells=True)
                 assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
                 assert np.max(np.abs(got[0].astype(np.float64) - ref[0])) <= (1e-4 if bil else 1e-5)
