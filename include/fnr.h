@@ -171,9 +171,16 @@ typedef struct {
      *   sigma [k^3] at (z*k + y)*k + x; negative and NaN densities are stored as 0
      *   uvw   [k^3][3D], channels u_1..u_D, v_1..v_D, w_1..w_D
      *   beta  [l][l][D] at (i_theta*l + i_phi)*D + i, sampled at bin centres
-     * FP16: round to nearest even. FP8: scale_c = absmax_c / 448 in binary32
-     * (1 if the channel is all zero), q = E4M3(x / scale_c), round to nearest
-     * even, saturating to +-448. */
+     * FP16: round to nearest even. FP8 (E4M3, round to nearest even, saturating
+     * to +-448): the density as one channel, scale_0 = absmax / 448 in binary32
+     * (1 if all zero), q = E4M3(sigma / scale_0). Each (u, v, w) channel c is
+     * stored as the residual from a per-brick offset: the grid is cut into
+     * offset bricks of Bo cells a side (the smallest power of two >= 4 with
+     * ceil(k / Bo) <= 64), and per brick the offset m is the binary16 (nearest
+     * even) value of the binary32 midrange (min + max) * 0.5 of the channel
+     * over the brick's cells (NaN ignored; 0 if all NaN); r = binary32(x - m),
+     * scale_c = absmax over the grid of |r| / 448 (1 if 0), q = E4M3(r /
+     * scale_c). The stored value is m + scale_c * e4m3(q). */
     const float *sigma;
     const float *uvw;
     const float *beta;
@@ -188,8 +195,9 @@ typedef struct {
 
 /* Bytes of the dense caches by the supplementary "Cache size calculation"
  * (second version, alpha = 1): k^3 (s_sigma + D s_uvw) + D s_beta l^2, where
- * s_uvw is one (u_i, v_i, w_i) triple; FP8 adds its (1 + 3D) binary32 scales.
- * Returns 0 for an invalid descriptor. */
+ * s_uvw is one (u_i, v_i, w_i) triple; FP8 adds its (1 + 3D) binary32 scales
+ * and its 3D binary16 offsets per offset brick. Returns 0 for an invalid
+ * descriptor. */
 FNR_API uint64_t fnr_cache_bytes(const fnr_cache_desc *desc);
 /* Device bytes one dense cache occupies: the above plus record padding to 16
  * bytes (8 for FP8), 256-byte section alignment, the two direction-bin tables
@@ -240,6 +248,10 @@ typedef struct {
                                       Used by FNR_RENDER_SKIP_EMPTY renders. [nj^3] bytes */
     int32_t distance_brick;    /* J */
     int32_t reserved2;
+    const uint16_t *offsets_dev; /* FP8: binary16 (u, v, w) offsets, offset brick (bz nbo + by) nbo + bx
+                                    at element offset_stride * brick + c, c < 3D; NULL otherwise */
+    int32_t offset_brick;      /* FP8: Bo (cells per side of an offset brick), else 0 */
+    int32_t offset_stride;     /* FP8: binary16 elements between bricks (3D rounded up to 8), else 0 */
 } fnr_cache_layout;
 FNR_API fnr_status fnr_cache_get_layout(const fnr_cache *cache, fnr_cache_layout *out);
 

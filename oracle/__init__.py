@@ -32,7 +32,8 @@ class _Cache(ctypes.Structure):
                 ("pos_prec", ctypes.c_int32), ("dir_prec", ctypes.c_int32),
                 ("sigma", ctypes.c_void_p), ("uvw", ctypes.c_void_p), ("beta", ctypes.c_void_p),
                 ("scales", ctypes.c_void_p), ("field", ctypes.c_void_p), ("field_user", ctypes.c_void_p),
-                ("occ", ctypes.c_void_p), ("occ_brick", ctypes.c_int32)]
+                ("occ", ctypes.c_void_p), ("occ_brick", ctypes.c_int32), ("off_brick", ctypes.c_int32),
+                ("offsets", ctypes.c_void_p)]
 
 
 class _Camera(ctypes.Structure):
@@ -73,6 +74,12 @@ def lib():
         L.orc_fp8_scale.restype = ctypes.c_float
         L.orc_quantize.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P, ctypes.c_int, ctypes.c_float, P]
         L.orc_quantize.restype = None
+        L.orc_fp8_offsets.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P]
+        L.orc_fp8_offsets.restype = None
+        L.orc_fp8_uvw_scale.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int]
+        L.orc_fp8_uvw_scale.restype = ctypes.c_float
+        L.orc_fp8_uvw_quantize.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P]
+        L.orc_fp8_uvw_quantize.restype = None
         for f in ("orc_bytes_nerf",):
             getattr(L, f).argtypes = [ctypes.c_uint64] * 4
             getattr(L, f).restype = ctypes.c_uint64
@@ -122,12 +129,14 @@ class Cache:
     uvw: [k^3, 3D] same dtype, channels u_1..u_D, v_1..v_D, w_1..w_D;
     beta: [l, l, D] float32 or uint16 FP16 bits, index [i_theta][i_phi];
     scales: float32 [1 + 3D] for FP8 (sigma first).
+    offsets: FP8 only, uint16 binary16 bits [nbo^3, 3D] of the (u, v, w) offsets per offset brick of
+    off_brick cells a side.
     field: optional (ctypes function pointer, user pointer) FP64 cell accessor
     that replaces sigma/uvw.
     """
 
     def __init__(self, k, D, l, sigma, uvw, beta, pos_prec=FP32, dir_prec=FP32, scales=None,
-                 bmin=(-1.5, -1.5, -1.5), bmax=(1.5, 1.5, 1.5), field=None):
+                 bmin=(-1.5, -1.5, -1.5), bmax=(1.5, 1.5, 1.5), field=None, offsets=None, off_brick=0):
         self.k, self.D, self.l = int(k), int(D), int(l)
         self.pos_prec, self.dir_prec = pos_prec, dir_prec
         self.sigma = None if sigma is None else np.ascontiguousarray(sigma).reshape(-1)
@@ -145,6 +154,10 @@ class Cache:
         s.uvw = None if self.uvw is None else self.uvw.ctypes.data
         s.beta = self.beta.ctypes.data
         s.scales = None if self.scales is None else self.scales.ctypes.data
+        self.offsets = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.uint16).reshape(-1)
+        self.off_brick = int(off_brick)
+        s.offsets = None if self.offsets is None else self.offsets.ctypes.data
+        s.off_brick = self.off_brick
         if field is not None:
             fn, user = field
             s.field = ctypes.cast(fn, ctypes.c_void_p).value
@@ -428,22 +441,40 @@ def fp8_scale(x: np.ndarray, clamp_nonneg: bool) -> float:
     return lib().orc_fp8_scale(x.size, 1, _p(x), int(clamp_nonneg))
 
 
+def offset_brick(k: int) -> int:
+    """Side of the E4M3 offset bricks: the smallest power of two >= 4 with ceil(k / Bo) <= 64."""
+    b = 4
+    while (k + b - 1) // b > 64:
+        b *= 2
+    return b
+
+
+def fp8_offsets(k, D, uvw, Bo) -> np.ndarray:
+    uvw = np.ascontiguousarray(uvw, dtype=np.float32).reshape(-1)
+    nbo = (k + Bo - 1) // Bo
+    out = np.zeros(nbo ** 3 * 3 * D, dtype=np.uint16)
+    lib().orc_fp8_offsets(k, 3 * D, Bo, _p(uvw), _p(out))
+    return out
+
+
 def quantize_cache(k, D, l, sigma, uvw, beta, pos_prec, dir_prec) -> Cache:
     """The oracle's own quantisation of FP32 cache arrays into a stored-precision Cache."""
     sigma = np.ascontiguousarray(sigma, dtype=np.float32).reshape(-1)
     uvw = np.ascontiguousarray(uvw, dtype=np.float32).reshape(-1, 3 * D)
     beta = np.ascontiguousarray(beta, dtype=np.float32).reshape(-1)
     scales = None
+    offsets, Bo = None, 0
     if pos_prec == FP8:
+        Bo = offset_brick(k)
+        offsets = fp8_offsets(k, D, uvw, Bo)
         scales = np.zeros(1 + 3 * D, dtype=np.float32)
         scales[0] = fp8_scale(sigma, True)
         for c in range(3 * D):
-            scales[1 + c] = lib().orc_fp8_scale(uvw.shape[0], 3 * D, _p(uvw[:, c:]), 0)
+            scales[1 + c] = lib().orc_fp8_uvw_scale(k, 3 * D, Bo, _p(uvw), _p(offsets), c)
         qs = quantize_channel(FP8, sigma, True, scales[0])
         qu = np.zeros(uvw.shape, dtype=np.uint8)
-        for c in range(3 * D):
-            col = np.ascontiguousarray(uvw[:, c])
-            qu[:, c] = quantize_channel(FP8, col, False, scales[1 + c])
+        lib().orc_fp8_uvw_quantize(k, 3 * D, Bo, _p(uvw), _p(offsets), _p(np.ascontiguousarray(scales[1:])),
+                                   _p(qu))
     elif pos_prec == FP16:
         qs = quantize_channel(FP16, sigma, True)
         qu = quantize_channel(FP16, uvw.reshape(-1), False).reshape(uvw.shape)
@@ -451,7 +482,8 @@ def quantize_cache(k, D, l, sigma, uvw, beta, pos_prec, dir_prec) -> Cache:
         qs = quantize_channel(FP32, sigma, True)
         qu = uvw
     qb = quantize_channel(FP16, beta, False) if dir_prec == FP16 else beta
-    return Cache(k, D, l, qs, qu, qb, pos_prec=pos_prec, dir_prec=dir_prec, scales=scales)
+    return Cache(k, D, l, qs, qu, qb, pos_prec=pos_prec, dir_prec=dir_prec, scales=scales, offsets=offsets,
+                 off_brick=Bo)
 
 
 # ------------------------------------------------------------------ cache sizes

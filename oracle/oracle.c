@@ -62,6 +62,8 @@ typedef struct {
     const uint8_t *occ;   /* optional: [nb^3] brick occupancy (nb = ceil(k / occ_brick)), brick
                              (bz nb + by) nb + bx nonzero iff one of its cells has sigma > 0 */
     int32_t occ_brick;    /* cells per brick side */
+    int32_t off_brick;    /* FP8 only: cells per side of an offset brick */
+    const uint16_t *offsets; /* FP8 only: [nbo^3][3D] binary16 offsets of the (u, v, w) channels */
 } orc_cache;
 
 typedef struct {
@@ -142,7 +144,9 @@ uint8_t orc_e4m3_encode(float f) {
 /* Cache quantisation as the precision forms define it: density is clamped
  * to >= 0 (NaN -> 0) first; FP8 uses one scale per channel,
  * scale = absmax / 448 in binary32 (1 when the channel is all zero), and
- * q = e4m3(x / scale) with a binary32 division. */
+ * q = e4m3(x / scale) with a binary32 division. For the (u, v, w) channels
+ * the quantised quantity is the residual from a per-brick offset
+ * (orc_fp8_offsets / orc_fp8_uvw_quantize below); the density has none. */
 float orc_fp8_scale(int64_t n, int64_t stride, const float *x, int clamp_nonneg) {
     float amax = 0.0f;
     for (int64_t i = 0; i < n; ++i) {
@@ -162,6 +166,66 @@ void orc_quantize(int prec, int64_t n, int64_t stride, const float *x, int clamp
         else if (prec == ORC_FP8) ((uint8_t *)out)[i * stride] = orc_e4m3_encode(v / scale);
         else ((float *)out)[i * stride] = v;
     }
+}
+
+/* E4M3 (u, v, w) offsets. The grid is cut into offset bricks of Bo cells a
+ * side (clipped to the grid; nbo = ceil(k / Bo) per axis, brick index
+ * (bz nbo + by) nbo + bx). Per brick and channel the offset is the binary16
+ * (nearest even) value of the binary32 midrange (min + max) * 0.5 of the
+ * channel's values over the brick's cells; NaN values are ignored, and a
+ * brick whose values are all NaN gets 0. out: [nbo^3][nch] binary16 bits. */
+void orc_fp8_offsets(int32_t k, int32_t nch, int32_t Bo, const float *uvw, uint16_t *out) {
+    const int64_t nbo = (k + Bo - 1) / Bo;
+    for (int64_t bz = 0; bz < nbo; ++bz)
+        for (int64_t by = 0; by < nbo; ++by)
+            for (int64_t bx = 0; bx < nbo; ++bx)
+                for (int c = 0; c < nch; ++c) {
+                    int any = 0;
+                    float mn = 0.0f, mx = 0.0f;
+                    for (int64_t z = bz * Bo; z < (bz + 1) * Bo && z < k; ++z)
+                        for (int64_t y = by * Bo; y < (by + 1) * Bo && y < k; ++y)
+                            for (int64_t x = bx * Bo; x < (bx + 1) * Bo && x < k; ++x) {
+                                const float v = uvw[((z * k + y) * k + x) * nch + c];
+                                if (v != v) continue;
+                                if (!any || v < mn) mn = v;
+                                if (!any || v > mx) mx = v;
+                                any = 1;
+                            }
+                    const float mid = any ? (mn + mx) * 0.5f : 0.0f;
+                    out[((bz * nbo + by) * nbo + bx) * nch + c] = orc_f16_encode(mid);
+                }
+}
+
+/* The offset of cell (x, y, z) in channel c, as binary32. */
+static float fp8_offset(int32_t k, int32_t nch, int32_t Bo, const uint16_t *offsets, int64_t cell, int c) {
+    const int64_t nbo = (k + Bo - 1) / Bo;
+    const int64_t x = cell % k, y = (cell / k) % k, z = cell / ((int64_t)k * k);
+    return (float)orc_f16_decode(offsets[(((z / Bo) * nbo + y / Bo) * nbo + x / Bo) * nch + c]);
+}
+
+/* Per-channel scale of the (u, v, w) residuals r = binary32(u - offset):
+ * absmax_c |r| / 448 in binary32 (NaN skipped; 1 when all are zero). */
+float orc_fp8_uvw_scale(int32_t k, int32_t nch, int32_t Bo, const float *uvw, const uint16_t *offsets, int c) {
+    const int64_t k3 = (int64_t)k * k * k;
+    float amax = 0.0f;
+    for (int64_t cell = 0; cell < k3; ++cell) {
+        const float r = uvw[cell * nch + c] - fp8_offset(k, nch, Bo, offsets, cell, c);
+        const float a = fabsf(r);
+        if (a > amax) amax = a;
+    }
+    return amax > 0.0f ? amax / 448.0f : 1.0f;
+}
+
+/* codes[cell][c] = E4M3(binary32(r / scale_c)), r = binary32(u - offset). The
+ * stored value is offset + scale_c * e4m3(q). */
+void orc_fp8_uvw_quantize(int32_t k, int32_t nch, int32_t Bo, const float *uvw, const uint16_t *offsets,
+                          const float *scales, uint8_t *codes) {
+    const int64_t k3 = (int64_t)k * k * k;
+    for (int64_t cell = 0; cell < k3; ++cell)
+        for (int c = 0; c < nch; ++c) {
+            const float r = uvw[cell * nch + c] - fp8_offset(k, nch, Bo, offsets, cell, c);
+            codes[cell * nch + c] = orc_e4m3_encode(r / scales[c]);
+        }
 }
 
 /* ------------------------------------------------------------ cache sizes */
@@ -296,8 +360,14 @@ static void cache_uvw(const orc_cache *c, int64_t cell, double *out) {
         return;
     }
     int n = 3 * c->D;
-    for (int j = 0; j < n; ++j)
-        out[j] = stored_scalar(c->pos_prec, c->uvw, cell * n + j, c->pos_prec == ORC_FP8 ? c->scales[1 + j] : 1.0f);
+    if (c->pos_prec == ORC_FP8) {
+        /* the exact value of the stored (code, scale, offset): offset + scale e4m3(code), FP64 */
+        for (int j = 0; j < n; ++j)
+            out[j] = orc_e4m3_decode(((const uint8_t *)c->uvw)[cell * n + j]) * (double)c->scales[1 + j] +
+                     (double)fp8_offset(c->k, n, c->off_brick, c->offsets, cell, j);
+        return;
+    }
+    for (int j = 0; j < n; ++j) out[j] = stored_scalar(c->pos_prec, c->uvw, cell * n + j, 1.0f);
 }
 
 /* ------------------------------------------------------------ cell table

@@ -76,7 +76,8 @@ class fnr_cache_layout(ctypes.Structure):
                 ("record_stride", ctypes.c_int32), ("occupancy_brick", ctypes.c_int32), ("footprint", ctypes.c_uint64),
                 ("layout", ctypes.c_int32), ("reserved1", ctypes.c_int32), ("page_table_dev", ctypes.c_void_p),
                 ("n_bricks", ctypes.c_uint64), ("brick_distance_dev", ctypes.c_void_p),
-                ("distance_brick", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("distance_brick", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("offsets_dev", ctypes.c_void_p), ("offset_brick", ctypes.c_int32), ("offset_stride", ctypes.c_int32)]
 
 
 class fnr_camera(ctypes.Structure):

@@ -45,7 +45,8 @@ int rec_stride_bytes(int prec, int D) {
 static uint64_t align256(uint64_t v) { return (v + 255u) & ~uint64_t(255u); }
 
 struct Layout {
-    uint64_t off_sigma, off_uvw, off_beta, off_ct, off_qp, off_scales, off_occ, off_dist, off_page, off_rank, total;
+    uint64_t off_sigma, off_uvw, off_beta, off_ct, off_qp, off_scales, off_offs, off_occ, off_dist, off_page, off_rank,
+        total;
     int rec_stride;
 };
 
@@ -60,6 +61,21 @@ int occupancy_shift(const fnr_cache_desc *d) {
     int sh = 1;
     while ((d->k + (1 << sh) - 1) >> sh > 64) ++sh;
     return sh;
+}
+
+int offset_shift(int k) {
+    int sh = 2;
+    while ((k + (1 << sh) - 1) >> sh > 64) ++sh;
+    return sh;
+}
+
+// binary16 elements per E4M3 offset brick: 3D rounded up to 8 (16-byte records)
+static int offset_stride(int D) { return (3 * D + 7) / 8 * 8; }
+
+static uint64_t offset_bytes(const fnr_cache_desc *d) {
+    if (d->pos_precision != FNR_PREC_FP8_E4M3) return 0;
+    const uint64_t nbo = uint64_t((d->k + (1 << offset_shift(d->k)) - 1) >> offset_shift(d->k));
+    return nbo * nbo * nbo * uint64_t(offset_stride(d->D)) * 2u;
 }
 
 // Jump-brick side of the distance field: the smallest power-of-two multiple of
@@ -111,6 +127,8 @@ static Layout layout_of(const fnr_cache_desc *d, int64_t n_bricks = -1) {
     off = align256(off + uint64_t(d->l) * 4);
     L.off_scales = off;
     off = align256(off + uint64_t(1 + 3 * d->D) * 4);
+    L.off_offs = off;
+    off = align256(off + offset_bytes(d));
     L.off_occ = off;
     off = align256(off + occupancy_words(d) * 4);
     L.off_dist = off;
@@ -195,18 +213,50 @@ static fnr_status build_from_arrays(fnr_cache *c, const fnr_cache_source *src, c
         *up = uu;
         return ee;
     };
+    const int osh = offset_shift(d.k), odim = (d.k + (1 << osh) - 1) >> osh, ostride = offset_stride(d.D);
+    uint16_t *offs = reinterpret_cast<uint16_t *>(base + L.off_offs);
     if (prec == FNR_PREC_FP8_E4M3) {
-        DevBuf amax;
+        // (1) per offset brick and channel the min and max, then the binary16 midranges; (2) the
+        // per-channel absmax of the density and of the residuals; (3) the scales
+        const int64_t nbo3 = int64_t(odim) * odim * odim;
+        DevBuf amax, kmm;
         if ((e = dev_malloc(&amax.p, sizeof(unsigned) * (1 + nch))) != cudaSuccess) return cuda_fail(e, "absmax");
-        if ((e = cudaMemsetAsync(amax.p, 0, sizeof(unsigned) * (1 + nch), s)) != cudaSuccess)
+        if ((e = dev_malloc(&kmm.p, sizeof(unsigned) * 2 * size_t(nbo3) * nch)) != cudaSuccess)
+            return cuda_fail(e, "offset min / max");
+        unsigned *kmin = static_cast<unsigned *>(kmm.p), *kmax = kmin + size_t(nbo3) * nch;
+        if ((e = cudaMemsetAsync(amax.p, 0, sizeof(unsigned) * (1 + nch), s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(kmin, 0xff, sizeof(unsigned) * size_t(nbo3) * nch, s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(kmax, 0, sizeof(unsigned) * size_t(nbo3) * nch, s)) != cudaSuccess)
             return cuda_fail(e, "memset");
         for (int64_t c0 = 0; c0 < k3; c0 += slab) {
             const int64_t n = std::min(slab, k3 - c0);
             const float *sp, *up;
             if ((e = slab_ptrs(c0, n, &sp, &up)) != cudaSuccess) return cuda_fail(e, "upload");
+            if ((e = launch_brick_minmax(up, c0, n, d.k, nch, osh, odim, kmin, kmax, s)) != cudaSuccess)
+                return cuda_fail(e, "offset min / max kernel");
+            if (!dev && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "min / max sync");
+        }
+        if ((e = launch_brick_offsets(kmin, kmax, nbo3, nch, offs, ostride, s)) != cudaSuccess)
+            return cuda_fail(e, "offsets kernel");
+        for (int64_t c0 = 0; c0 < k3; c0 += slab) {
+            const int64_t n = std::min(slab, k3 - c0);
+            const float *sp, *up;
+            if ((e = slab_ptrs(c0, n, &sp, &up)) != cudaSuccess) return cuda_fail(e, "upload");
+            // the density channel (and the raw absmax of the others, overwritten below)
             if ((e = launch_absmax(sp, up, n, nch, static_cast<unsigned *>(amax.p), s)) != cudaSuccess)
                 return cuda_fail(e, "absmax kernel");
             if (!dev && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "absmax sync");
+        }
+        if ((e = cudaMemsetAsync(static_cast<unsigned *>(amax.p) + 1, 0, sizeof(unsigned) * nch, s)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+        for (int64_t c0 = 0; c0 < k3; c0 += slab) {
+            const int64_t n = std::min(slab, k3 - c0);
+            const float *sp, *up;
+            if ((e = slab_ptrs(c0, n, &sp, &up)) != cudaSuccess) return cuda_fail(e, "upload");
+            if ((e = launch_residual_absmax(up, c0, n, d.k, nch, offs, osh, odim, ostride,
+                                            static_cast<unsigned *>(amax.p), s)) != cudaSuccess)
+                return cuda_fail(e, "residual absmax kernel");
+            if (!dev && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "residual sync");
         }
         if ((e = launch_scales_from_absmax(static_cast<unsigned *>(amax.p), scales, 1 + nch, s)) != cudaSuccess)
             return cuda_fail(e, "scales kernel");
@@ -220,7 +270,7 @@ static fnr_status build_from_arrays(fnr_cache *c, const fnr_cache_source *src, c
             cudaSuccess)
             return cuda_fail(e, "density conversion");
         if ((e = launch_convert_uvw(up, base + L.off_uvw + c0 * L.rec_stride, n, d.D, prec, L.rec_stride, scales,
-                                    s)) != cudaSuccess)
+                                    s, offs, c0, d.k, osh, odim, ostride)) != cudaSuccess)
             return cuda_fail(e, "uvw conversion");
         if (!dev && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "conversion sync");
     }
@@ -252,6 +302,11 @@ static void fill_view(fnr_cache *c, const Layout &L) {
     v.scales = reinterpret_cast<const float *>(base + L.off_scales);
     v.occ = reinterpret_cast<const uint32_t *>(base + L.off_occ);
     v.dist = reinterpret_cast<const uint8_t *>(base + L.off_dist);
+    const bool fp8 = d.pos_precision == FNR_PREC_FP8_E4M3;
+    v.offs = fp8 ? reinterpret_cast<const uint16_t *>(base + L.off_offs) : nullptr;
+    v.offs_shift = fp8 ? offset_shift(d.k) : 0;
+    v.offs_dim = fp8 ? (d.k + (1 << v.offs_shift) - 1) >> v.offs_shift : 0;
+    v.offs_stride = fp8 ? offset_stride(d.D) : 0;
     v.layout = c->n_bricks > 0 || d.layout == FNR_LAYOUT_BRICKS ? FNR_LAYOUT_BRICKS : FNR_LAYOUT_DENSE;
     v.page = v.layout == FNR_LAYOUT_BRICKS ? reinterpret_cast<const int32_t *>(base + L.off_page) : nullptr;
     v.rank = v.layout == FNR_LAYOUT_BRICKS ? reinterpret_cast<const uint32_t *>(base + L.off_rank) : nullptr;
@@ -400,7 +455,10 @@ uint64_t fnr_cache_bytes(const fnr_cache_desc *d) {
     const uint64_t s_beta = elem_bytes(d->dir_precision) * 8u;
     uint64_t bits = (uint64_t(d->D) * s_uvw + s_sigma) * k3 + uint64_t(d->D) * s_beta * d->l * d->l;
     uint64_t bytes = bits / 8u;
-    if (d->pos_precision == FNR_PREC_FP8_E4M3) bytes += uint64_t(1 + 3 * d->D) * 4u;
+    if (d->pos_precision == FNR_PREC_FP8_E4M3) {
+        const uint64_t nbo = uint64_t((d->k + (1 << offset_shift(d->k)) - 1) >> offset_shift(d->k));
+        bytes += uint64_t(1 + 3 * d->D) * 4u + nbo * nbo * nbo * uint64_t(3 * d->D) * 2u;
+    }
     return bytes;
 }
 
@@ -745,6 +803,9 @@ fnr_status fnr_cache_get_layout(const fnr_cache *c, fnr_cache_layout *out) {
     out->brick_distance_dev = v.dist;
     out->distance_brick = 1 << v.dist_shift;
     out->reserved2 = 0;
+    out->offsets_dev = v.offs;
+    out->offset_brick = v.offs ? 1 << v.offs_shift : 0;
+    out->offset_stride = v.offs ? v.offs_stride : 0;
     out->n_bricks = c->n_bricks;
     out->footprint = c->footprint;
     return FNR_OK;

@@ -21,6 +21,7 @@ struct CacheView {
     const float *ct;      // [l] cos(theta_j) boundaries
     const float *qp;      // [l] azimuth-key boundaries
     const float *scales;  // FP8: [1 + 3D]
+    const uint16_t *offs; // FP8: binary16 (u, v, w) offsets, [offs_dim^3][offs_stride]
     const uint32_t *occ;  // brick occupancy bits, brick (bz * occ_dim + by) * occ_dim + bx
     const int32_t *page;  // FNR_LAYOUT_BRICKS: brick -> pool slot (-1 empty); sigma / uvw are the pools
     const uint32_t *rank; // FNR_LAYOUT_BRICKS: set occupancy bits in the words before each word
@@ -28,6 +29,9 @@ struct CacheView {
                           // capped at kDistCap + 1
     int32_t occ_shift;    // log2 of the brick side in cells
     int32_t occ_dim;      // bricks per axis, ceil(k / 2^occ_shift)
+    int32_t offs_shift;   // FP8: log2 of the offset-brick side in cells
+    int32_t offs_dim;     // FP8: offset bricks per axis
+    int32_t offs_stride;  // FP8: binary16 elements per offset brick (3D rounded up to 8)
     int32_t dist_shift;   // log2 of the jump-brick side in cells (>= occ_shift)
     int32_t dist_dim;     // jump bricks per axis, ceil(k / 2^dist_shift) <= kDistMaxDim
     int32_t layout;       // FNR_LAYOUT_*
@@ -119,7 +123,19 @@ cudaError_t launch_gather_bricks(const void *sigma, const char *uvw, void *sigma
 cudaError_t launch_convert_sigma(const float *in, void *out, int64_t n, int prec, const float *scale,
                                  cudaStream_t s);
 cudaError_t launch_convert_uvw(const float *in, char *out, int64_t n_cells, int D, int prec, int rec_stride,
-                               const float *scales, cudaStream_t s);
+                               const float *scales, cudaStream_t s, const uint16_t *offs = nullptr,
+                               int64_t c0 = 0, int k = 0, int oshift = 0, int odim = 0, int ostride = 0);
+// E4M3 (u, v, w) offsets: the smallest power of two >= 4 with ceil(k / Bo) <= 64, as a shift.
+int offset_shift(int k);
+// Per offset brick and channel: running min / max of a slab of cells c0 .. c0 + n (order-preserving
+// uint keys; initialise with 0xffffffff / 0), then the binary16 midranges.
+cudaError_t launch_brick_minmax(const float *uvw, int64_t c0, int64_t n, int k, int nch, int oshift, int odim,
+                                unsigned *kmin, unsigned *kmax, cudaStream_t s);
+cudaError_t launch_brick_offsets(const unsigned *kmin, const unsigned *kmax, int64_t n_bricks, int nch,
+                                 uint16_t *offs, int ostride, cudaStream_t s);
+// Per-channel absmax of the residuals from the offsets (atomicMax on the bits of |r|, amax_bits[1 + c]).
+cudaError_t launch_residual_absmax(const float *uvw, int64_t c0, int64_t n, int k, int nch, const uint16_t *offs,
+                                   int oshift, int odim, int ostride, unsigned *amax_bits, cudaStream_t s);
 cudaError_t launch_convert_beta(const float *in, void *out, int64_t n, int prec, cudaStream_t s);
 cudaError_t launch_absmax(const float *sigma, const float *uvw, int64_t n_cells, int nch, unsigned *amax_bits,
                           cudaStream_t s);

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC)) march_kernel
     tile_origin(F, t, x0, y0);
     const int lane = threadIdx.x & 31;
     const int px = x0 + (lane & (kTileW - 1)), py = y0 + lane / kTileW;
-    __shared__ WarpQueue<D> queues[FNR_BLOCK / 32];
+    __shared__ QueueFor<PREC, D> queues[FNR_BLOCK / 32];
     march_tile_queued<PREC, D, SKIP, BRICKS>(A.c, A.r, F, px, py, px < F.W && py < F.H, queues[threadIdx.x >> 5]);
 }
 

@@ -30,7 +30,7 @@ namespace dev {
 #define FNR_MINB_FP16 8
 #endif
 #ifndef FNR_MINB_FP8
-#define FNR_MINB_FP8 8
+#define FNR_MINB_FP8 7
 #endif
 #ifndef FNR_FAST_EXP
 #define FNR_FAST_EXP 1
@@ -110,7 +110,58 @@ struct Record<FNR_PREC_FP8_E4M3, D> {
         unsigned int word = ((i >> 2) & 1) ? q.y : q.x;
         return e4m3_to_float((word >> (8 * (i & 3))) & 0xffu);
     }
+    // codes 2p and 2p + 1 with one paired conversion
+    __device__ __forceinline__ float2 get2(int p) const {
+        const uint2 &q = v[p >> 2];
+        const unsigned int word = ((p >> 1) & 1) ? q.y : q.x;
+        const __nv_fp8x2_storage_t two = static_cast<__nv_fp8x2_storage_t>((word >> (16 * (p & 1))) & 0xffffu);
+        return __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(two, __NV_E4M3)));
+    }
 };
+
+// The binary16 (u, v, w) offsets of one E4M3 offset brick (3D values, 16-byte aligned).
+template <int D>
+struct OffsetRecord {
+    static constexpr int NV = (3 * D + 7) / 8;
+    uint4 v[NV];
+    __device__ __forceinline__ void load(const uint16_t *p) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = __ldg(reinterpret_cast<const uint4 *>(p) + j);
+    }
+    __device__ __forceinline__ float get(int i) const {
+        const uint4 &q = v[i >> 3];
+        const int w = (i >> 1) & 3;
+        const unsigned int word = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
+        return __half2float(__ushort_as_half(static_cast<unsigned short>((i & 1) ? (word >> 16) : (word & 0xffffu))));
+    }
+};
+
+// E4M3 colour (Eq. 5 on the stored values): component i = ch D + j is
+// u_i = fma(s_i, e4m3(q_i), m_i) (its channel scale s_i and offset m_i), and
+// x_ch = sum_j beta_j u_{ch D + j} in the order j = 0 .. D-1; scale_of(i) and
+// beta_of(j) supply s_i and beta_j.
+template <int D, class ScaleOf, class BetaOf>
+__device__ __forceinline__ void shade_e4m3(const Record<FNR_PREC_FP8_E4M3, D> &rec, const OffsetRecord<D> &off,
+                                           int act, ScaleOf scale_of, BetaOf beta_of, float col[3]) {
+    float x[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int p = 0; p < (3 * D + 1) / 2; ++p) {
+        const float2 q = rec.get2(p);
+        const int i = 2 * p;
+        x[i / D] = __fmaf_rn(beta_of(i % D), __fmaf_rn(scale_of(i), q.x, off.get(i)), x[i / D]);
+        if (i + 1 < 3 * D)
+            x[(i + 1) / D] =
+                __fmaf_rn(beta_of((i + 1) % D), __fmaf_rn(scale_of(i + 1), q.y, off.get(i + 1)), x[(i + 1) / D]);
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+#if FNR_FAST_EXP
+        col[ch] = act == FNR_ACT_IDENTITY ? x[ch] : __fdividef(1.0f, 1.0f + __expf(-x[ch]));
+#else
+        col[ch] = act == FNR_ACT_IDENTITY ? x[ch] : 1.0f / (1.0f + expf(-x[ch]));
+#endif
+    }
+}
 
 template <int PREC>
 __device__ __forceinline__ float load_sigma(const CacheView &c, int cell, float sigma_scale) {
@@ -468,7 +519,9 @@ __device__ __forceinline__ void extinction(float od, float &ext, float &alpha) {
 // binary32 result equals the sequential form bit for bit.
 constexpr int kQCap = 32 * (kUnroll + 1);  // entries left after a flush (< 32) plus one group's appends
 
-template <int D>
+// OFFS (E4M3 caches): each entry also carries its offset brick, and the warp
+// keeps the 3D channel scales.
+template <int D, bool OFFS = false>
 struct WarpQueue {
     int cell[kQCap];
     float w[kQCap];
@@ -476,7 +529,11 @@ struct WarpQueue {
     float col[3][32];
     float beta[D][32];     // beta of each lane's ray (unscaled)
     unsigned int own_mask[32];
+    int obr[OFFS ? kQCap : 1];  // offset brick of each entry
+    float sc[OFFS ? 3 * D : 1]; // scale of (u, v, w) channel ch D + j
 };
+template <int PREC, int D>
+using QueueFor = WarpQueue<D, PREC == FNR_PREC_FP8_E4M3>;
 
 // SKIP (FNR_RENDER_SKIP_EMPTY): a sample in a brick without stored density is
 // known to be empty, so only samples in occupied bricks load their density; the
@@ -486,7 +543,8 @@ struct WarpQueue {
 // among the occupied bricks, and the queue carries pool indices instead of cells.
 template <int PREC, int D, bool SKIP, bool BRICKS = false>
 __device__ __forceinline__ void march_tile_queued(const CacheView &c, const RenderConst &r, const FrameDesc &F,
-                                                  int px, int py, bool active, WarpQueue<D> &q) {
+                                                  int px, int py, bool active, QueueFor<PREC, D> &q) {
+    constexpr bool kOffs = PREC == FNR_PREC_FP8_E4M3;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     RaySetup<PREC, D> R;
@@ -499,6 +557,10 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
     }
     if (!active)
         for (int i = 0; i < D; ++i) q.beta[i][lane] = 0.0f;
+    if constexpr (kOffs) {
+        for (int i = lane; i < 3 * D; i += 32) q.sc[i] = __ldg(c.scales + 1 + i);
+        __syncwarp();
+    }
     float T = 1.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
     long long S = 0;
     int n_look = 0, n_occ = 0, n_steps = r.N;
@@ -521,16 +583,11 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
             own = q.owner[e];
             Record<PREC, D> rec;
             rec.load(c.uvw + static_cast<long long>(q.cell[e]) * c.rec_stride);
-            if constexpr (PREC == FNR_PREC_FP8_E4M3) {
-                // scaled beta formed at its use: keeps 3D products out of registers
-                float bj = 0.0f;
-                RaySetup<PREC, D>::shade_with(
-                    rec, r.act,
-                    [&](int ch, int j) {
-                        if (ch == 0) bj = q.beta[j][own];  // read once per component
-                        return bj * __ldg(c.scales + 1 + ch * D + j);
-                    },
-                    col);
+            if constexpr (kOffs) {
+                OffsetRecord<D> off;
+                off.load(c.offs + static_cast<long long>(q.obr[e]) * c.offs_stride);
+                shade_e4m3<D>(
+                    rec, off, r.act, [&](int i) { return q.sc[i]; }, [&](int j) { return q.beta[j][own]; }, col);
             } else {
                 float b[D];
 #pragma unroll
@@ -753,6 +810,15 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
                 q.cell[pos] = cell[u];
                 q.w[pos] = aw[u];
                 q.owner[pos] = static_cast<unsigned char>(lane);
+                if constexpr (kOffs) {
+                    // the sample's offset brick, from its cell coordinates
+                    const float fu = __fadd_rn(static_cast<float>(i0 + u), 0.5f);
+                    const int sh = c.offs_shift;
+                    const int ox = __float2int_rd(__fmaf_rn(fu, R.e[0], R.f[0])) >> sh;
+                    const int oy = __float2int_rd(__fmaf_rn(fu, R.e[1], R.f[1])) >> sh;
+                    const int oz = __float2int_rd(__fmaf_rn(fu, R.e[2], R.f[2])) >> sh;
+                    q.obr[pos] = (oz * c.offs_dim + oy) * c.offs_dim + ox;
+                }
                 ++pos;
             }
         }
@@ -766,6 +832,7 @@ __device__ __forceinline__ void march_tile_queued(const CacheView &c, const Rend
                 q.cell[lane] = q.cell[base + lane];
                 q.w[lane] = q.w[base + lane];
                 q.owner[lane] = q.owner[base + lane];
+                if constexpr (kOffs) q.obr[lane] = q.obr[base + lane];
             }
             __syncwarp();
             qn = rem;

@@ -77,10 +77,11 @@ struct VoxelWalk {
         tn2 = crossing(c2, u2, w2);
     }
 
-    // The current cell, its occupancy brick (bricks of 2^sh cells, od per axis)
-    // and its length; advances to the next cell, or clears live after the last
-    // one. The step is branch-free: lanes of a warp step different axes.
-    __device__ __forceinline__ int next(float &delta, int &brick, int sh, int od) {
+    // The current cell, its occupancy brick (bricks of 2^sh cells, od per axis),
+    // its E4M3 offset brick (2^osh cells, odim per axis) and its length;
+    // advances to the next cell, or clears live after the last one. The step is
+    // branch-free: lanes of a warp step different axes.
+    __device__ __forceinline__ int next(float &delta, int &brick, int sh, int od, int &obrick, int osh, int odim) {
         int a = 0;
         float tnext = tn0;
         if (tn1 < tnext) {
@@ -94,6 +95,7 @@ struct VoxelWalk {
         const float end = tnext < t1 ? tnext : t1;
         const int cell = (c2 * k + c1) * k + c0;  // k^3 < 2^31
         brick = ((c2 >> sh) * od + (c1 >> sh)) * od + (c0 >> sh);
+        obrick = ((c2 >> osh) * odim + (c1 >> osh)) * odim + (c0 >> osh);
         delta = __fsub_rn(end, t);
         if (!(tnext < t1)) {
             live = false;
@@ -133,8 +135,15 @@ __global__ void __launch_bounds__(FNR_BLOCK) march_voxels_kernel(const __grid_co
     const int lane = threadIdx.x & 31;
     const int px = x0 + (lane & (kTileW - 1)), py = y0 + lane / kTileW;
     const bool active = px < F.W && py < F.H;
+    constexpr bool kOffs = PREC == FNR_PREC_FP8_E4M3;
     __shared__ float sbeta[FNR_BLOCK / 32][D][32];
+    __shared__ float wsc[FNR_BLOCK / 32][kOffs ? 3 * D : 1];  // E4M3: the (u, v, w) channel scales, per warp
     float (*qbeta)[32] = sbeta[threadIdx.x >> 5];
+    float *ssc = wsc[threadIdx.x >> 5];
+    if constexpr (kOffs) {
+        for (int i = lane; i < 3 * D; i += 32) ssc[i] = __ldg(c.scales + 1 + i);
+        __syncwarp();
+    }
 
     RaySetup<PREC, D> R;  // a1/a2: direction cell and beta (the uniform-sample fields go unused)
     VoxelWalk Wk;
@@ -166,16 +175,17 @@ __global__ void __launch_bounds__(FNR_BLOCK) march_voxels_kernel(const __grid_co
 
     while (__any_sync(FULL, Wk.live && !term && n_gen < r.N)) {
         // kVU cells ahead, their densities loaded together
-        int cell[kVU], brick[kVU];
+        int cell[kVU], brick[kVU], obr[kVU];
         float dl[kVU], sg[kVU];
         unsigned gen = 0u, looked = 0u;
 #pragma unroll
         for (int u = 0; u < kVU; ++u) {
             cell[u] = 0;
             brick[u] = 0;
+            obr[u] = 0;
             dl[u] = 0.0f;
             if (Wk.live && !term && n_gen < r.N) {
-                cell[u] = Wk.next(dl[u], brick[u], c.occ_shift, c.occ_dim);
+                cell[u] = Wk.next(dl[u], brick[u], c.occ_shift, c.occ_dim, obr[u], c.offs_shift, c.offs_dim);
                 gen |= 1u << u;
                 ++n_gen;
             }
@@ -221,14 +231,14 @@ __global__ void __launch_bounds__(FNR_BLOCK) march_voxels_kernel(const __grid_co
             Record<PREC, D> rec;
             rec.load(c.uvw + static_cast<long long>(cell[u]) * c.rec_stride);
             float col[3];
-            RaySetup<PREC, D>::shade_with(
-                rec, r.act,
-                [&](int ch, int j) {
-                    const float b = qbeta[j][lane];
-                    if constexpr (PREC == FNR_PREC_FP8_E4M3) return b * __ldg(c.scales + 1 + ch * D + j);
-                    return b;
-                },
-                col);
+            if constexpr (kOffs) {
+                OffsetRecord<D> off;
+                off.load(c.offs + static_cast<long long>(obr[u]) * c.offs_stride);
+                shade_e4m3<D>(
+                    rec, off, r.act, [&](int i) { return ssc[i]; }, [&](int j) { return qbeta[j][lane]; }, col);
+            } else {
+                RaySetup<PREC, D>::shade_with(rec, r.act, [&](int ch, int j) { return qbeta[j][lane]; }, col);
+            }
             Cr = __fmaf_rn(wgt[u], col[0], Cr);
             Cg = __fmaf_rn(wgt[u], col[1], Cg);
             Cb = __fmaf_rn(wgt[u], col[2], Cb);

@@ -50,7 +50,7 @@ int g_grid[kMaxDevices][3][17] = {};
 template <int PREC, int D>
 __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
     noalloc_kernel(const __grid_constant__ MarchArgs A, unsigned int *scratch, uint32_t *done_words) {
-    __shared__ dev::WarpQueue<D> queues[FNR_BLOCK / 32];
+    __shared__ dev::QueueFor<PREC, D> queues[FNR_BLOCK / 32];
     const int lane = threadIdx.x & 31;
     for (;;) {
         int t = 0;

@@ -4,7 +4,8 @@
 // Densities are clamped to >= 0 (NaN -> 0) before storage. FP16 rounds to
 // nearest even; FP8 stores E4M3(x / scale_c) rounded to nearest even and
 // saturated to +-448, scale_c = absmax_c / 448 (binary32 division; 1 for an
-// all-zero channel). The (u, v, w) records are padded to rec_stride bytes with
+// all-zero channel). For the (u, v, w) channels x is the residual from the
+// cell's offset brick: the binary16 midrange of the channel over the brick. The (u, v, w) records are padded to rec_stride bytes with
 // zeros so every record starts on a 16-byte (FP8: 8-byte) boundary.
 // The brick occupancy bits are derived from the stored densities with the
 // march's own dequantisation, so "brick empty" means exactly that every
@@ -31,6 +32,86 @@ unsigned grid_for(int64_t n, int threads) {
     return static_cast<unsigned>(b < 1 ? 1 : b);
 }
 
+// Order-preserving uint key of a binary32 value (NaN excluded by the callers).
+__device__ __forceinline__ unsigned order_key(float v) {
+    const unsigned b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float from_order_key(unsigned o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// Offset brick of cell index `cell` (x fastest): (z >> sh, y >> sh, x >> sh).
+__device__ __forceinline__ int64_t offset_brick_of(int64_t cell, int k, int sh, int dim) {
+    const int64_t x = cell % k, y = (cell / k) % k, z = cell / (static_cast<int64_t>(k) * k);
+    return ((z >> sh) * dim + (y >> sh)) * dim + (x >> sh);
+}
+
+// One thread per cell of the slab, all channels; lanes of a warp whose cells
+// share an offset brick combine their keys first, so each (warp, brick,
+// channel) makes one atomic min and one atomic max.
+__global__ void brick_minmax_kernel(const float *__restrict__ uvw, int64_t c0, int64_t n, int k, int nch, int sh,
+                                    int dim, unsigned *__restrict__ kmin, unsigned *__restrict__ kmax) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t n_iter = (n + stride - 1) / stride;  // the same trip count for every lane (warp-wide sync)
+    const int64_t first = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (int64_t it = 0; it < n_iter; ++it) {
+        const int64_t i = first + it * stride;
+        const bool in = i < n;
+        const long long b = in ? offset_brick_of(c0 + i, k, sh, dim) : -1;
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        const bool leader = in && (threadIdx.x & 31) == __ffs(same) - 1;
+        for (int c = 0; c < nch; ++c) {
+            const float v = in ? uvw[i * nch + c] : 0.0f;
+            const bool ok = in && v == v;
+            const unsigned lo = __reduce_min_sync(same, ok ? order_key(v) : 0xffffffffu);
+            const unsigned hi = __reduce_max_sync(same, ok ? order_key(v) : 0u);
+            if (leader) {
+                if (lo != 0xffffffffu) atomicMin(kmin + b * nch + c, lo);
+                if (hi != 0u) atomicMax(kmax + b * nch + c, hi);
+            }
+        }
+    }
+}
+
+// Offsets: the binary16 (nearest even) value of (min + max) * 0.5 in binary32, 0 for a brick
+// whose values were all NaN; the padding of each offset record is 0.
+__global__ void brick_offsets_kernel(const unsigned *__restrict__ kmin, const unsigned *__restrict__ kmax,
+                                     int64_t n_bricks, int nch, uint16_t *__restrict__ offs, int ostride) {
+    const int64_t total = n_bricks * ostride;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = e / ostride;
+        const int c = static_cast<int>(e - b * ostride);
+        float m = 0.0f;
+        if (c < nch && kmin[b * nch + c] != 0xffffffffu)
+            m = (from_order_key(kmin[b * nch + c]) + from_order_key(kmax[b * nch + c])) * 0.5f;
+        offs[e] = __half_as_ushort(__float2half_rn(m));
+    }
+}
+
+__device__ __forceinline__ float offset_of(const uint16_t *__restrict__ offs, int64_t cell, int c, int k, int sh,
+                                           int dim, int ostride) {
+    return __half2float(__ushort_as_half(offs[offset_brick_of(cell, k, sh, dim) * ostride + c]));
+}
+
+// Per-channel absmax of |binary32(u - offset)| (NaN skipped) into amax_bits[1 + c].
+__global__ void residual_absmax_kernel(const float *__restrict__ uvw, int64_t c0, int64_t n, int k, int nch,
+                                       const uint16_t *__restrict__ offs, int sh, int dim, int ostride,
+                                       unsigned *__restrict__ amax_bits) {
+    __shared__ unsigned smax[3 * FNR_MAX_D];
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) smax[c] = 0u;
+    __syncthreads();
+    const int64_t total = n * nch;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / nch;
+        const int c = static_cast<int>(e - i * nch);
+        const float r = fabsf(uvw[e] - offset_of(offs, c0 + i, c, k, sh, dim, ostride));
+        if (r == r) atomicMax(&smax[c], __float_as_uint(r));
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) atomicMax(&amax_bits[1 + c], smax[c]);
+}
+
 __global__ void convert_sigma_kernel(const float *__restrict__ in, void *__restrict__ out, int64_t n, int prec,
                                      const float *__restrict__ scale) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -44,7 +125,9 @@ __global__ void convert_sigma_kernel(const float *__restrict__ in, void *__restr
 // One thread per output byte-group would waste bandwidth on the padding; one
 // thread per (cell, channel) element, padding written by channel-0 threads.
 __global__ void convert_uvw_kernel(const float *__restrict__ in, char *__restrict__ out, int64_t n_cells, int nch,
-                                   int prec, int rec_stride, const float *__restrict__ scales) {
+                                   int prec, int rec_stride, const float *__restrict__ scales,
+                                   const uint16_t *__restrict__ offs, int64_t c0, int k, int sh, int dim,
+                                   int ostride) {
     const int64_t total = n_cells * nch;
     const int es = prec == FNR_PREC_FP32 ? 4 : prec == FNR_PREC_FP16 ? 2 : 1;
     const int pad_bytes = rec_stride - nch * es;
@@ -55,7 +138,9 @@ __global__ void convert_uvw_kernel(const float *__restrict__ in, char *__restric
         const float v = in[e];
         if (prec == FNR_PREC_FP32) reinterpret_cast<float *>(rec)[ch] = v;
         else if (prec == FNR_PREC_FP16) reinterpret_cast<__half *>(rec)[ch] = __float2half_rn(v);
-        else reinterpret_cast<unsigned char *>(rec)[ch] = to_e4m3(__fdiv_rn(v, scales[1 + ch]));
+        else
+            reinterpret_cast<unsigned char *>(rec)[ch] =
+                to_e4m3(__fdiv_rn(__fsub_rn(v, offset_of(offs, c0 + cell, ch, k, sh, dim, ostride)), scales[1 + ch]));
         if (ch == 0)
             for (int b = 0; b < pad_bytes; ++b) rec[nch * es + b] = 0;
     }
@@ -230,10 +315,34 @@ cudaError_t launch_convert_sigma(const float *in, void *out, int64_t n, int prec
 }
 
 cudaError_t launch_convert_uvw(const float *in, char *out, int64_t n_cells, int D, int prec, int rec_stride,
-                               const float *scales, cudaStream_t s) {
+                               const float *scales, cudaStream_t s, const uint16_t *offs, int64_t c0, int k,
+                               int oshift, int odim, int ostride) {
     if (n_cells <= 0) return cudaSuccess;
+    if (prec == FNR_PREC_FP8_E4M3 && !offs) return cudaErrorInvalidValue;
     convert_uvw_kernel<<<grid_for(n_cells * 3 * D, 256), 256, 0, s>>>(in, out, n_cells, 3 * D, prec, rec_stride,
-                                                                        scales);
+                                                                        scales, offs, c0, k, oshift, odim, ostride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_minmax(const float *uvw, int64_t c0, int64_t n, int k, int nch, int oshift, int odim,
+                                unsigned *kmin, unsigned *kmax, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    brick_minmax_kernel<<<grid_for(n, 256), 256, 0, s>>>(uvw, c0, n, k, nch, oshift, odim, kmin, kmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_offsets(const unsigned *kmin, const unsigned *kmax, int64_t n_bricks, int nch,
+                                 uint16_t *offs, int ostride, cudaStream_t s) {
+    if (n_bricks <= 0) return cudaSuccess;
+    brick_offsets_kernel<<<grid_for(n_bricks * ostride, 256), 256, 0, s>>>(kmin, kmax, n_bricks, nch, offs, ostride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_absmax(const float *uvw, int64_t c0, int64_t n, int k, int nch, const uint16_t *offs,
+                                   int oshift, int odim, int ostride, unsigned *amax_bits, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    residual_absmax_kernel<<<grid_for(n * nch, 256), 256, 0, s>>>(uvw, c0, n, k, nch, offs, oshift, odim, ostride,
+                                                                   amax_bits);
     return cudaGetLastError();
 }
 

@@ -86,7 +86,7 @@ template <int PREC, int D, bool SKIP, bool BRICKS>
 __global__ void __launch_bounds__(FNR_BLOCK, dev::min_blocks(PREC))
     serve_kernel(const __grid_constant__ ServeTable tab, ServeScratch *scr, volatile uint32_t *done_flags) {
     constexpr int kWarps = FNR_BLOCK / 32;
-    __shared__ dev::WarpQueue<D> queues[kWarps];
+    __shared__ dev::QueueFor<PREC, D> queues[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int total = tab.total_tiles;
     const int nf = tab.n_frames;

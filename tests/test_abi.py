@@ -78,7 +78,8 @@ def test_cache_bytes_paper_integers(fnr):
     d32 = fnr.make_desc(1024, 8, 1024, fnr.FNR_PREC_FP32, fnr.FNR_PREC_FP32)
     assert fnr.fnr_cache_bytes(d32) == 2 * (c["pos_bytes"] + c["dir_bytes"])
     d8 = fnr.make_desc(1024, 8, 1024, fnr.FNR_PREC_FP8_E4M3, fnr.FNR_PREC_FP16)
-    assert fnr.fnr_cache_bytes(d8) == c["pos_bytes"] // 2 + c["dir_bytes"] + 25 * 4
+    # E4M3 adds 25 binary32 scales and 24 binary16 offsets per offset brick (16 cells a side at k = 1024)
+    assert fnr.fnr_cache_bytes(d8) == c["pos_bytes"] // 2 + c["dir_bytes"] + 25 * 4 + 64 ** 3 * 24 * 2
 
 
 def test_cache_footprint_and_invalid_desc(fnr):

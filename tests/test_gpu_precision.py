@@ -6,7 +6,9 @@ unquantised binary32 field.
 Bars: with the FP16 cache every integer output (steps, lookups, occupied samples, direction cell) is
 bit-exact, because this scene family's densities (0 and 50) are exact in FP16; colour error is the
 cache quantisation error: FP16 max abs <= 5e-3 and PSNR >= 60 dB (11-bit significands on |u| <~ 4,
-|beta| <~ 3, through a sigmoid); E4M3 (4-bit significands) PSNR >= 40 dB.
+|beta| <~ 3, through a sigmoid). E4M3 stores each (u, v, w) value as a 4-bit-significand residual
+from its offset brick's binary16 midrange; the residuals span about a third of the values' range, so
+E4M3 PSNR >= 50 dB and max abs <= 2e-2 (without the offsets, per-channel scales alone gave 44.5 dB).
 """
 
 import numpy as np
@@ -77,4 +79,6 @@ def test_precision_k1024_sampled_parity():
         assert np.max(np.abs(c16 - ref)) <= 5e-3
         assert psnr(c16[:, :3], ref[:, :3]) >= 60.0
         img8, _ = got["fp8"]
-        assert psnr(img8[i][py, px, :3], ref[:, :3]) >= 40.0
+        c8 = img8[i][py, px, :3]
+        assert psnr(c8, ref[:, :3]) >= 50.0, f"view {i}: E4M3 PSNR {psnr(c8, ref[:, :3]):.2f} dB"
+        assert np.max(np.abs(c8 - ref[:, :3])) <= 2e-2

@@ -114,6 +114,13 @@ def test_tiny_parity(fnr, ctx, tiny_workload, tiny_arrays, prec, dprec, on_devic
         assert np.array_equal(device_bytes(lay.beta_dev, w.l * w.l * w.D * bes), oc.beta.view(np.uint8))
         if prec == 2:
             assert np.array_equal(device_bytes(lay.scales_dev, (1 + 3 * w.D) * 4).view(np.float32), oc.scales)
+            # binary16 (u, v, w) offsets per offset brick, each brick's record padded to offset_stride
+            assert lay.offset_brick == oc.off_brick
+            nbo3 = (-(-w.k // oc.off_brick)) ** 3
+            offs = device_bytes(lay.offsets_dev, nbo3 * lay.offset_stride * 2).view(np.uint16)
+            offs = offs.reshape(nbo3, lay.offset_stride)
+            assert np.array_equal(offs[:, :3 * w.D], oc.offsets.reshape(nbo3, 3 * w.D))
+            assert not offs[:, 3 * w.D:].any()
         cam = w.cameras()[0]
         p = fnr.make_params(w.n_samples)
         got = gpu_render(fnr, ctx, cache, [cam], p, with_cells=True)[0]

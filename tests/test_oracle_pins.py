@@ -492,9 +492,17 @@ def test_fp8_scale_and_codes_by_definition():
         assert np.all(np.abs(dec - y) <= step / 2 * (1 + 1e-12))
 
 
-def test_fp8_cache_clamps_density_only():
-    """quantize_cache: the density plane is clamped before its scale is taken, the (u, v, w) channels are
-    not (their negative values set their scales and keep their sign); scales[0] belongs to the density."""
+def test_fp8_cache_by_hand():
+    """quantize_cache for E4M3: the density plane is clamped and scaled as one channel (no offset); each
+    (u, v, w) channel is stored as the residual from its offset brick's binary16 midrange, one binary32 scale
+    per channel = absmax residual / 448.
+
+    k = 2 (one offset brick of Bo = 4 cells). Channel 0 = {0, 1.5, -7, 3.5, 0, 0, 0, 0}: midrange
+    (-7 + 3.5) / 2 = -1.75, residuals {1.75, 3.25, -5.25, 5.25, 1.75, ...}, scale 5.25 / 448 = 3/256;
+    r / scale = {149.33, 277.33, -448, 448, 149.33, ...} -> codes {0x71 (144: exponent field 14,
+    mantissa 1), 0x79 (288: exponent field 15, mantissa 1), 0xFE, 0x7E, 0x71, ...}. Channel 1 = {-2, 0, ...}:
+    midrange -1, residuals {-1, 1, ...}, scale 1/448, codes {0xFE, 0x7E, ...}. Channel 2 all zero: offset 0,
+    scale 1, codes 0. The stored value of cell 0, channel 0 is -1.75 + 144 * 3/256 = -0.0625."""
     k, D, l = 2, 1, 2
     sig = np.array([0, 1.5, -7, 3.5, 0, 0, 0, 0], np.float32)
     uvw = np.zeros((8, 3), np.float32)
@@ -502,12 +510,69 @@ def test_fp8_cache_clamps_density_only():
     uvw[0, 1] = -2.0
     beta = np.ones((l * l, D), np.float32)
     q = oracle.quantize_cache(k, D, l, sig, uvw, beta, oracle.FP8, oracle.FP16)
-    assert q.scales[0] == 2.0 ** -7 and q.scales[1] == 2.0 ** -6
-    assert q.scales[2] == np.float32(2.0 / 448.0) and q.scales[3] == 1.0
-    assert list(np.asarray(q.sigma)[:4]) == [0x00, 0x74, 0x00, 0x7E]
+    assert q.off_brick == 4
+    assert list(q.offsets) == [0xBF00, 0xBC00, 0x0000]  # binary16 -1.75, -1, 0
+    assert q.scales[0] == 2.0 ** -7 and q.scales[1] == 3.0 / 256 and q.scales[3] == 1.0
+    assert q.scales[2] == np.float32(np.float32(1.0) / np.float32(448.0))
+    assert list(np.asarray(q.sigma)) == [0x00, 0x74, 0x00, 0x7E, 0, 0, 0, 0]
     qu = np.asarray(q.uvw).reshape(8, 3)
-    assert list(qu[:4, 0]) == [0x00, 0x6C, 0xFE, 0x76]
-    assert qu[0, 1] == 0xFE
+    assert list(qu[:, 0]) == [0x71, 0x79, 0xFE, 0x7E, 0x71, 0x71, 0x71, 0x71]
+    assert list(qu[:, 1]) == [0xFE] + [0x7E] * 7
+    assert list(qu[:, 2]) == [0] * 8
+    # the oracle renders the exact stored value: with density only in cell 0, identity activation and
+    # beta = 1, a ray through cell 0 has colour (stored u, v, w of cell 0) (1 - T) + T bg
+    sig1 = np.array([50, 0, 0, 0, 0, 0, 0, 0], np.float32)
+    q1 = oracle.quantize_cache(k, D, l, sig1, uvw, beta, oracle.FP8, oracle.FP16)
+    s1 = np.asarray(q1.scales, np.float64)
+    stored = [-1.75 + s1[1] * 144, -1.0 - s1[2] * 448, 0.0]
+    cam = dict(c2w=np.array([1, 0, 0, -0.75, 0, 1, 0, -0.75, 0, 0, 1, 4], np.float32), fx=np.float32(10.0),
+               fy=np.float32(10.0), cx=np.float32(0.5), cy=np.float32(0.5), W=1, H=1)
+    bg = (0.25, 0.5, 0.75)
+    rgba, st, _ = oracle.render_pixels(q1, cam, oracle.params_struct(64, 2.0, 6.0, 0.0, bg, oracle.ACT_IDENTITY),
+                                       [0], [0])
+    m = st[0, 2]
+    assert m == 24  # samples at z = 2 - (i + 1/2) / 16 inside [-1.5, 0): i = 32 .. 55
+    sigma_stored = float(np.float32(448.0) * np.float32(s1[0]))  # binary32 product of code 0x7E and the scale
+    T = math.exp(-sigma_stored * m / 16)                          # Delta = 4 / 64
+    np.testing.assert_allclose(rgba[0, :3], np.array(stored) * (1 - T) + T * np.array(bg), rtol=0, atol=1e-12)
+    assert oracle.offset_brick(64) == 4 and oracle.offset_brick(256) == 4 and oracle.offset_brick(512) == 8
+    assert oracle.offset_brick(1024) == 16 and oracle.offset_brick(1290) == 32
+
+
+def test_fp8_offsets_and_residual_bound():
+    """Any grid: each offset is the binary16 value of a number between the brick's min and max (so the
+    residuals of a brick straddle 0), the largest residual of each channel codes to +-448, and every stored
+    value (offset + scale * e4m3(code)) is within half an E4M3 step (times the scale) of the input."""
+    rng = np.random.default_rng(4)
+    for k, D in ((6, 2), (9, 1), (16, 3)):
+        uvw = (rng.standard_normal((k ** 3, 3 * D)) * 3 + rng.uniform(-5, 5, 3 * D)).astype(np.float32)
+        sig = np.abs(rng.standard_normal(k ** 3)).astype(np.float32)
+        q = oracle.quantize_cache(k, D, 4, sig, uvw, np.ones((16, D), np.float32), oracle.FP8, oracle.FP32)
+        Bo = q.off_brick
+        nbo = -(-k // Bo)
+        off = oracle.f16_decode(q.offsets).reshape(nbo, nbo, nbo, 3 * D)
+        idx = np.arange(k ** 3)
+        x, y, z = idx % k, (idx // k) % k, idx // (k * k)
+        m = off[z // Bo, y // Bo, x // Bo]            # [k^3, 3D] offset of each cell
+        U = uvw.reshape(k, k, k, 3 * D)
+        for bz in range(nbo):
+            for by in range(nbo):
+                for bx in range(nbo):
+                    blk = U[bz * Bo:(bz + 1) * Bo, by * Bo:(by + 1) * Bo, bx * Bo:(bx + 1) * Bo].reshape(-1, 3 * D)
+                    o = off[bz, by, bx]
+                    assert np.all(o >= blk.min(0) - np.abs(blk.min(0)) * 2 ** -10)
+                    assert np.all(o <= blk.max(0) + np.abs(blk.max(0)) * 2 ** -10)
+        codes = np.asarray(q.uvw).reshape(k ** 3, 3 * D)
+        dec = oracle.e4m3_decode(codes.reshape(-1)).reshape(codes.shape)
+        r = (uvw - m.astype(np.float32)).astype(np.float32).astype(np.float64)
+        s = q.scales[1:].astype(np.float64)
+        for c in range(3 * D):
+            a = int(np.argmax(np.abs(r[:, c])))
+            assert codes[a, c] == (0xFE if r[a, c] < 0 else 0x7E)
+        y_ = np.abs(r / s)
+        step = np.where(y_ < 2 ** -6, 2.0 ** -9, 2.0 ** (np.floor(np.log2(np.maximum(y_, 2 ** -6))) - 3))
+        stored = m + s * dec
+        assert np.all(np.abs(stored - uvw) <= (step / 2) * s * (1 + 1e-6) + 1e-12)
 
 
 def test_build_sample_points_by_hand():
