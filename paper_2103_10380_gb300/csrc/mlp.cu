@@ -245,6 +245,15 @@ __device__ __forceinline__ uint32_t a_offset(int row, int k) {
                     ((((k >> 3) & 7) ^ (row & 7)) << 4) + (k & 7) * 2);
 }
 
+// ReLU(a), ReLU(b) rounded to bf16 (nearest even) and packed, a in the low
+// half, in one conversion; a negative value rounds to a negative bf16, so
+// clamping after rounding equals rounding after clamping.
+__device__ __forceinline__ uint32_t pack_relu_bf16(float a, float b) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat16 x = __float2bfloat16_rn(a), y = __float2bfloat16_rn(b);
     return uint32_t(__bfloat16_as_ushort(x)) | (uint32_t(__bfloat16_as_ushort(y)) << 16);
@@ -398,8 +407,8 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
     if (warp == kProducerWarp) {
         if (lane == 0) {
             long long it = 0;
-            long long issued[kSlots];  // per slot: the round of its last bulk copy (-1: none in flight)
-            for (int sl = 0; sl < kSlots; ++sl) issued[sl] = -1;
+            static_assert(kSlots == 2, "the producer tracks two ring slots");
+            long long issued0 = -1, issued1 = -1;  // per slot: the round of its last bulk copy (-1: none)
             for (long long r = 0; r < n_pairs && !abort_flag; ++r)
                 for (int li = 0; li < A.n_layers && !abort_flag; ++li)
                     for (int t = 0; t < kPair && !abort_flag; ++t) {
@@ -416,13 +425,14 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                             mbar_expect_tx(full_bar(slot), bytes);
                             const char *src = reinterpret_cast<const char *>(Ly.w) + size_t(c) * Ly.N * kChunkK * 2;
                             bulk_g2s(smem_u32(ring) + uint32_t(slot) * kSlotBytes, src, bytes, full_bar(slot));
-                            issued[slot] = round;
+                            if (slot == 0) issued0 = round;
+                            else issued1 = round;
                         }
                     }
             // Every copy issued has landed before the CTA's shared memory goes away
             // (after an abort some may not have been waited for).
-            for (int sl = 0; sl < kSlots; ++sl)
-                if (issued[sl] >= 0) mbar_drain(full_bar(sl), uint32_t(issued[sl] & 1), A.err);
+            if (issued0 >= 0) mbar_drain(full_bar(0), uint32_t(issued0 & 1), A.err);
+            if (issued1 >= 0) mbar_drain(full_bar(1), uint32_t(issued1 & 1), A.err);
         }
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
@@ -526,14 +536,10 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                                                       ? *reinterpret_cast<const float4 *>(bias + c0 + u + 4)
                                                       : __ldg(reinterpret_cast<const float4 *>(bias + c0 + u + 4));
                                 uint4 pk;
-                                pk.x = pack_bf16(fmaxf(__uint_as_float(rr[u + 0]) + b0.x, 0.0f),
-                                                 fmaxf(__uint_as_float(rr[u + 1]) + b0.y, 0.0f));
-                                pk.y = pack_bf16(fmaxf(__uint_as_float(rr[u + 2]) + b0.z, 0.0f),
-                                                 fmaxf(__uint_as_float(rr[u + 3]) + b0.w, 0.0f));
-                                pk.z = pack_bf16(fmaxf(__uint_as_float(rr[u + 4]) + b1.x, 0.0f),
-                                                 fmaxf(__uint_as_float(rr[u + 5]) + b1.y, 0.0f));
-                                pk.w = pack_bf16(fmaxf(__uint_as_float(rr[u + 6]) + b1.z, 0.0f),
-                                                 fmaxf(__uint_as_float(rr[u + 7]) + b1.w, 0.0f));
+                                pk.x = pack_relu_bf16(__uint_as_float(rr[u + 0]) + b0.x, __uint_as_float(rr[u + 1]) + b0.y);
+                                pk.y = pack_relu_bf16(__uint_as_float(rr[u + 2]) + b0.z, __uint_as_float(rr[u + 3]) + b0.w);
+                                pk.z = pack_relu_bf16(__uint_as_float(rr[u + 4]) + b1.x, __uint_as_float(rr[u + 5]) + b1.y);
+                                pk.w = pack_relu_bf16(__uint_as_float(rr[u + 6]) + b1.z, __uint_as_float(rr[u + 7]) + b1.w);
                                 *reinterpret_cast<uint4 *>(sa_t + a_offset(row, c0 + u)) = pk;
                             }
                         };
