@@ -213,20 +213,43 @@ __device__ __forceinline__ float phi_key(float x, float y) {
     return __fadd_rn(3.0f, __fdiv_rn(x, __fadd_rn(x, -y)));
 }
 
-// Direction cell: counts of boundaries passed; the libm estimate only picks
-// where the exact walk over the (monotone) tables starts.
+// Starting estimates for the direction cell; the exact walk over the boundary
+// tables corrects any error, so short polynomial approximations suffice.
+// Polar angle: acos(x) ~ sqrt(1 - x) (a0 + a1 x + a2 x^2 + a3 x^3) for
+// 0 <= x <= 1 (Abramowitz & Stegun, Handbook of Mathematical Functions,
+// 4.4.45; |error| <= 7e-5 rad), acos(-x) = pi - acos(x).
+__device__ __forceinline__ float acos_estimate(float x) {
+    const float ax = fminf(fabsf(x), 1.0f);
+    const float p = fmaf(fmaf(fmaf(-0.0187293f, ax, 0.0742610f), ax, -0.2121144f), ax, 1.5707288f);
+    const float a = sqrtf(1.0f - ax) * p;
+    return x < 0.0f ? 3.14159265f - a : a;
+}
+// Azimuth from the diamond key q in [0, 4]: quadrant floor(q), and inside it
+// the angle pi/4 + atan(2 t - 1) for t = q - floor(q) (tan of the angle is
+// t / (1 - t)); atan(z) ~ (pi/4) z - z (|z| - 1)(0.2447 + 0.0663 |z|) on
+// [-1, 1] (Rajan, Wang, Inkol and Joyal, "Efficient approximations for the
+// arctangent function", IEEE Signal Processing Magazine 23(3), 2006;
+// |error| <= 1.5e-3 rad).
+__device__ __forceinline__ float azimuth_estimate(float q) {
+    const float k = floorf(fminf(q, 3.999999f));
+    const float z = 2.0f * (q - k) - 1.0f;
+    const float az = fabsf(z);
+    const float at = fmaf(0.78539816f, z, -z * (az - 1.0f) * fmaf(0.0663f, az, 0.2447f));
+    return fmaf(1.57079633f, k, 0.78539816f + at);
+}
+
+// Direction cell: counts of boundaries passed; the estimates only pick where
+// the exact walk over the (monotone) tables starts.
 __device__ __forceinline__ int dir_cell(const CacheView &c, float dx, float dy, float dz) {
     const int l = c.l;
     const float inv_pi = 0.318309886183790671538f;
-    int it = static_cast<int>(acosf(fminf(fmaxf(dz, -1.0f), 1.0f)) * inv_pi * static_cast<float>(l));
+    int it = static_cast<int>(acos_estimate(dz) * inv_pi * static_cast<float>(l));
     it = min(max(it, 0), l - 1);
     while (it < l - 1 && dz <= __ldg(c.ct + it + 1)) ++it;
     while (it > 0 && dz > __ldg(c.ct + it)) --it;
-    float ph = atan2f(dy, dx);
-    if (ph < 0.0f) ph += 6.28318530717958647692f;
-    int ip = static_cast<int>(ph * (0.5f * inv_pi) * static_cast<float>(l));
-    ip = min(max(ip, 0), l - 1);
     const float q = phi_key(dx, dy);
+    int ip = static_cast<int>(azimuth_estimate(q) * (0.5f * inv_pi) * static_cast<float>(l));
+    ip = min(max(ip, 0), l - 1);
     while (ip < l - 1 && q >= __ldg(c.qp + ip + 1)) ++ip;
     while (ip > 0 && q < __ldg(c.qp + ip)) --ip;
     return it * l + ip;
