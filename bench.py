@@ -456,6 +456,7 @@ def uncached_render(fnr, torch, dev, w, reps=3):
 
 
 RATES = (50.0, 100.0, 200.0, 400.0, 2000.0, 5000.0)
+CLOSED_LOOP_REQUESTS = 1200
 
 
 def serving_config(fnr, torch, dev, w, sig, uvw, beta, seconds, rates=RATES, seed=11, budget=120e9, repeats=2):
@@ -467,7 +468,7 @@ def serving_config(fnr, torch, dev, w, sig, uvw, beta, seconds, rates=RATES, see
     launch, one request at a time in arrival order (latency counts the wait for earlier requests).
     Each rate is run `repeats` times with fresh draws (p50/p99 per repeat, and their median / spread).
     The two highest rates load the GPU enough that launches batch several requests. Then closed loop
-    (every request of a 400 req/s draw submitted at once) for throughput."""
+    (1200 requests drawn like the 400 req/s ones, submitted at once) for throughput."""
     import scenegen
     ctx = fnr.fnr_context_create(dev.index or 0, int(budget))
     params = fnr.make_params(w.n_samples, w.t_near, w.t_far, w.t_thr, w.bg)
@@ -497,8 +498,8 @@ def serving_config(fnr, torch, dev, w, sig, uvw, beta, seconds, rates=RATES, see
         used[key] += 1
         return t
 
-    def workload(rate, rng):
-        n = max(8, int(rate * seconds))
+    def workload(rate, rng, n=None):
+        n = max(8, int(rate * seconds)) if n is None else n
         reqs = []
         for i in range(n):
             W, H = RESOLUTIONS[int(rng.integers(0, len(RESOLUTIONS)))]
@@ -553,7 +554,9 @@ def serving_config(fnr, torch, dev, w, sig, uvw, beta, seconds, rates=RATES, see
     fnr.fnr_serve_start(ctx, n_slots=3, max_batch_requests=64, use_graphs=1, idle_spin_us=-1)
     torch.cuda.synchronize(dev)
     rng = np.random.default_rng(seed)
-    warm, _ = workload(200.0, rng)
+    # the untimed warm-up and the closed loop submit every request at once: fixed sizes within the
+    # request queue's capacity (4096 pending requests), whatever the seconds per rate
+    warm, _ = workload(200.0, rng, n=600)
     for form in ("fp16", "fp8_e4m3"):
         run_served(form, warm, None)  # graphs captured, kernels loaded
     run_plain(warm, None)
@@ -569,7 +572,7 @@ def serving_config(fnr, torch, dev, w, sig, uvw, beta, seconds, rates=RATES, see
             runs["plain_fp32_per_frame"].append(summary(*run_plain(reqs, arrivals), len(reqs)))
         row = {"requests": n_req, "repeats": repeats, **{key: combine(v) for key, v in runs.items()}}
         res[f"{int(rate)}_req_per_s"] = row
-    reqs, _ = workload(400.0, rng)
+    reqs, _ = workload(400.0, rng, n=CLOSED_LOOP_REQUESTS)
     row = {"requests": len(reqs)}
     for form in ("fp16", "fp8_e4m3"):
         row["served_" + form] = summary(*run_served(form, reqs, None), len(reqs))

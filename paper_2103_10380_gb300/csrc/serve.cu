@@ -217,6 +217,7 @@ struct Server {
     std::vector<Slot> slots;
     std::thread th;
     bool stop = false;
+    bool abandon = false;  // at process exit: drop the queued requests, finish only the launched batches
     uint64_t next_ticket = 1;
     int64_t next_batch = 0;
     fnr_status fatal = FNR_OK;
@@ -331,6 +332,7 @@ struct Server {
 
     // Queued requests -> free slots, in arrival order, one kernel key per batch.
     bool admit_locked() {
+        if (abandon) return false;
         bool progress = false;
         for (Slot &s : slots) {
             if (s.busy || pending.empty()) continue;
@@ -408,7 +410,7 @@ struct Server {
         for (;;) {
             bool busy = false;
             for (Slot &s : slots) busy |= s.busy;
-            if (stop && pending.empty() && !busy) break;
+            if (stop && (pending.empty() || abandon) && !busy) break;
             const bool p1 = poll_locked();
             const bool p2 = admit_locked();
             busy = false;
@@ -432,6 +434,58 @@ struct Server {
         }
     }
 };
+
+// Request loops still running when the process exits. Their threads poll
+// pinned host memory and CUDA events, which the CUDA runtime releases when it
+// shuts down at exit; a thread still polling then crashes the process. The
+// guard below is constructed at the first loop start, after the runtime has
+// initialised, so its destructor runs before the runtime's shutdown (exit
+// handlers run in reverse order of registration): it drops the queued
+// requests of every live loop, lets the launched batches finish and joins the
+// threads. Resources are left to the process's end.
+constexpr int kMaxLiveLoops = 256;
+
+struct LiveLoops {
+    std::mutex mu;
+    Server *sv[kMaxLiveLoops] = {};
+
+    ~LiveLoops() {
+        std::lock_guard<std::mutex> g(mu);
+        for (Server *&s : sv) {
+            if (!s) continue;
+            {
+                std::lock_guard<std::mutex> l(s->mu);
+                s->stop = true;
+                s->abandon = true;
+            }
+            s->cv_sched.notify_all();
+            if (s->th.joinable()) s->th.join();
+            s = nullptr;
+        }
+    }
+};
+
+static LiveLoops &live_loops() {
+    static LiveLoops loops;
+    return loops;
+}
+
+static void live_add(Server *s) {
+    LiveLoops &L = live_loops();
+    std::lock_guard<std::mutex> g(L.mu);
+    for (Server *&e : L.sv)
+        if (!e) {
+            e = s;
+            return;
+        }
+}
+
+static void live_remove(Server *s) {
+    LiveLoops &L = live_loops();
+    std::lock_guard<std::mutex> g(L.mu);
+    for (Server *&e : L.sv)
+        if (e == s) e = nullptr;
+}
 
 static fnr_status server_start(fnr_context *ctx, const fnr_serve_config *cfg_in) {
     fnr_serve_config cfg;
@@ -483,7 +537,9 @@ static fnr_status server_start(fnr_context *ctx, const fnr_serve_config *cfg_in)
         delete sv;
         return st;
     }
+    live_loops();  // the exit guard exists before the thread does
     sv->th = std::thread([sv] { sv->loop(); });
+    live_add(sv);
     ctx->server = sv;
     return FNR_OK;
 }
@@ -496,7 +552,8 @@ void server_stop(fnr_context *ctx) {
         sv->stop = true;
     }
     sv->cv_sched.notify_all();
-    sv->th.join();
+    live_remove(sv);
+    if (sv->th.joinable()) sv->th.join();
     cudaSetDevice(ctx->device);
     for (Slot &s : sv->slots) {
         cudaStreamSynchronize(s.stream);

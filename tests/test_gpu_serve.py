@@ -251,3 +251,45 @@ def test_scheduler_idle_spin(fnr, scenes, idle_spin_us):
         fnr.fnr_serve_stop(ctx)
     finally:
         fnr.fnr_context_destroy(ctx)
+
+
+EXIT_SCRIPT = r"""
+import sys
+import torch
+import scenegen
+import paper_2103_10380_gb300 as fnr
+w = scenegen.tiny()
+sig, uvw = scenegen.fill_position_grid(w.scene, w.k)
+beta = scenegen.direction_grid(w.scene, w.l)
+ctx = fnr.fnr_context_create(0, 0)
+cache = fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, 0, 0), sig.reshape(-1), uvw.reshape(-1),
+                            beta.reshape(-1))
+fnr.fnr_serve_start(ctx, queue_capacity=16 if sys.argv[1] == "queue_full" else 0, n_slots=2, idle_spin_us=-1)
+outs = [torch.zeros(64 * 48 * 4, device="cuda") for _ in range(8)]
+cams = scenegen.cameras(5, 8, 64, 48)
+p = fnr.make_params(w.n_samples)
+for i in range(10000):
+    fnr.fnr_submit(ctx, fnr.make_request(cache, cams[i % 8], p, outs[i % 8]))
+    if i == 40 and sys.argv[1] == "exit":
+        sys.exit(0)
+"""
+
+
+@pytest.mark.parametrize("how", ["exit", "queue_full"])
+def test_process_exit_with_live_loop(fnr, how):
+    """A process that ends with its request loop still running (never stopped, requests queued and in
+    flight) ends cleanly: by sys.exit, or by an uncaught QUEUE_FULL error from a burst larger than the
+    queue. The loop's thread is stopped before the CUDA runtime shuts down, so the exit status is the
+    program's own, never a crash."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    r = subprocess.run([sys.executable, "-c", EXIT_SCRIPT, how], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=600)
+    if how == "exit":
+        assert r.returncode == 0, r.stderr[-2000:]
+    else:
+        assert r.returncode == 1, r.stderr[-2000:]
+        assert "QUEUE_FULL" in r.stderr
