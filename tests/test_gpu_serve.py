@@ -261,16 +261,20 @@ import paper_2103_10380_gb300 as fnr
 w = scenegen.tiny()
 sig, uvw = scenegen.fill_position_grid(w.scene, w.k)
 beta = scenegen.direction_grid(w.scene, w.l)
-ctx = fnr.fnr_context_create(0, 0)
-cache = fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, 0, 0), sig.reshape(-1), uvw.reshape(-1),
-                            beta.reshape(-1))
+desc = fnr.make_desc(w.k, w.D, w.l, 0, 0)
+req_bytes = 64 * 48 * 16
+# queue_full: a budget that holds the cache and leaves one byte less than a request needs, so no
+# request is ever admitted and the queue fills; exit: no budget
+budget = fnr.fnr_cache_footprint(desc) + req_bytes - 1 if sys.argv[1] == "queue_full" else 0
+ctx = fnr.fnr_context_create(0, budget)
+cache = fnr.fnr_build_cache(ctx, desc, sig.reshape(-1), uvw.reshape(-1), beta.reshape(-1))
 fnr.fnr_serve_start(ctx, queue_capacity=16, n_slots=1, idle_spin_us=-1)
 outs = [torch.zeros(64 * 48 * 4, device="cuda") for _ in range(8)]
 cams = scenegen.cameras(5, 8, 64, 48)
 p = fnr.make_params(w.n_samples)
 side = torch.cuda.Stream()
 with torch.cuda.stream(side):
-    torch.cuda._sleep(500_000_000)  # the outputs' stream is busy for a while: the one slot's batch waits on it
+    torch.cuda._sleep(500_000_000)  # a bounded spin on the outputs' stream: the first batch waits behind it
 for i in range(10000):
     fnr.fnr_submit(ctx, fnr.make_request(cache, cams[i % 8], p, outs[i % 8], stream=side))
     if i == 8 and sys.argv[1] == "exit":
@@ -280,11 +284,10 @@ for i in range(10000):
 
 @pytest.mark.parametrize("how", ["exit", "queue_full"])
 def test_process_exit_with_live_loop(fnr, how):
-    """A process that ends with its request loop still running (never stopped; a batch launched and
-    waiting on the outputs' stream, which a bounded GPU sleep keeps busy, and requests queued behind it)
-    ends cleanly: by sys.exit, or by the uncaught QUEUE_FULL error of a burst larger than the queue. The
-    loop's thread is stopped before the CUDA runtime shuts down, so the exit status is the program's own,
-    never a crash."""
+    """A process that ends with its request loop still running (never stopped, requests launched or
+    queued) ends cleanly: by sys.exit, or by the uncaught QUEUE_FULL error of a burst that the HBM budget
+    keeps from being admitted. The loop's thread is stopped before the CUDA runtime shuts down, so the
+    exit status is the program's own, never a crash."""
     import os
     import subprocess
     import sys
