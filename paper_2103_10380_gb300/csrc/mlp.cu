@@ -3,12 +3,18 @@
 // Section 3.2 Eqs. 3-4 and Section 4: F_pos and F_dir are ReLU MLPs on
 // positionally encoded inputs).
 //
-// One CTA per SM walks tiles of 128 grid points with four warp roles:
-//   producer (warp 0): streams every layer's bf16 weights, pre-arranged in
-//     64-column K chunks of the K-major 128-byte swizzled operand layout,
-//     through a 2-slot shared-memory ring by bulk async copy (cp.async.bulk,
-//     completion on the slot's "full" mbarrier), running ahead across layers
-//     and tiles;
+// A pair of CTAs on two SMs (a cluster of two) walks tiles of 256 grid points,
+// each CTA holding 128 of them; rank 0 issues M = 256 MMAs for the pair
+// (tcgen05.mma.cta_group::2) that read each CTA's A rows and each CTA's half of
+// the weight chunk from that CTA's own shared memory and accumulate into each
+// CTA's own tensor memory. Each SM therefore streams half of every weight chunk
+// per MMA tile. Warp roles, in both CTAs:
+//   producer (warp 0): streams this CTA's half of every layer's bf16 weights,
+//     pre-arranged in 64-column K chunks of the K-major 128-byte swizzled
+//     operand layout, through a 4-slot shared-memory ring by bulk async copy
+//     (cp.async.bulk, completion on the slot's "full" mbarrier), running ahead
+//     across layers and tiles; rank 0's producer passes each slot's release on
+//     to rank 1;
 //   two tiles are in flight: each has its own A tile (same swizzled layout)
 //     and its own tensor-memory accumulator, so one tile's epilogue runs while
 //     the other's MMAs do;
@@ -16,11 +22,12 @@
 //     pi x), rounded to bf16) into the tile's layer-0 staging buffer one tile
 //     pair ahead, as soon as the MMAs that read the buffer's previous contents
 //     have completed, so encoding never waits between tiles;
-//   MMA issuer (warp 1, one lane): waits for the layer input and each chunk,
-//     issues tcgen05.mma (M=128, N=layer width, K=16 steps, bf16 x bf16 ->
-//     fp32 in tensor memory; layer 0 reads the staging buffer), releases each
-//     slot with tcgen05.commit on its "empty" mbarrier and signals the
-//     finished accumulator with one more commit;
+//   MMA issuer (warp 1, one lane of rank 0): waits for both CTAs' layer inputs
+//     and chunk halves, issues tcgen05.mma (M=256, N=layer width, K=16 steps,
+//     bf16 x bf16 -> fp32 in tensor memory; layer 0 reads the staging
+//     buffers), releases each slot with tcgen05.commit on its "empty" mbarrier
+//     and signals the finished accumulators with one more commit; in rank 1
+//     the same lane tells rank 0 when each chunk half has landed;
 //   epilogue (warps 4-19, four per 32-lane quarter of tensor memory): per
 //     hidden layer read the accumulator (tcgen05.ld), add the bias, apply
 //     ReLU, round to bf16 and write the next layer's A tile; after the head,
@@ -28,11 +35,16 @@
 //     tile's sigma = ReLU(out_0), (u, v, w) = out_1..3D (F_pos) or beta =
 //     out_0..D-1 (F_dir) -- contiguous ranges of the cache -- with coalesced
 //     stores by all sixteen warps.
-// The next layer's weights load while the epilogue runs. Every mbarrier wait
-// is bounded; a wait that runs out sets the error word and a CTA-wide abort
-// flag, every role leaves its loop, the producer waits (bounded) for the copies
-// it has in flight, the MMA issuer for its tensor-core operations, and the
-// tensor memory is freed.
+// Rank 0 issues each tcgen05.commit twice, on its own copy of the barrier and,
+// through the barrier's cluster address, on rank 1's; rank 1's threads arrive
+// on rank 0's barriers with remote mbarrier arrives, and rank 1 reports each
+// landed chunk half the same way. The next layer's weights load while the
+// epilogue runs. Every mbarrier wait is bounded; a wait that runs
+// out sets the error word and both CTAs' abort flags, every role leaves its
+// loop, each producer waits (bounded) for the copies it has in flight, the
+// MMA issuer for its tensor-core operations (rank 1 for the same commit), and
+// the tensor memory is freed. Built with FNR_MLP_CTAS=1 the kernel is the
+// single-CTA form: M = 128 MMAs, whole chunks through a 2-slot ring.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -51,8 +63,21 @@ constexpr int kTileM = 128;
 constexpr int kMaxK = 256;
 constexpr int kMaxN = 256;
 constexpr int kChunkK = 64;                          // K columns per weight chunk: one 128-byte swizzle row
+#ifndef FNR_MLP_CTAS
+#define FNR_MLP_CTAS 1
+#endif
+// CTAs per MMA: 2 = a cluster of two CTAs on an SM pair issuing M = 256 MMAs
+// (cta_group::2), each CTA holding 128 rows of A and half of every weight chunk.
+constexpr int kCtas = FNR_MLP_CTAS;
+static_assert(kCtas == 1 || kCtas == 2, "CTAs per MMA");
+#if FNR_MLP_CTAS == 2
+#define FNR_CTA_GROUP "cta_group::2"
+#else
+#define FNR_CTA_GROUP "cta_group::1"
+#endif
+constexpr int kSuperM = kTileM * kCtas;              // points per MMA tile
 #ifndef FNR_MLP_SLOTS
-#define FNR_MLP_SLOTS 2
+#define FNR_MLP_SLOTS (2 * FNR_MLP_CTAS)
 #endif
 #ifndef FNR_MLP_PAIR
 #define FNR_MLP_PAIR 2
@@ -61,7 +86,7 @@ constexpr int kChunkK = 64;                          // K columns per weight chu
 #define FNR_MLP_BIAS_SMEM 0
 #endif
 constexpr int kSlots = FNR_MLP_SLOTS;                // ring slots
-constexpr int kSlotBytes = kMaxN * kChunkK * 2;      // 32 KB
+constexpr int kSlotBytes = kMaxN / kCtas * kChunkK * 2;  // this CTA's rows of one weight chunk
 constexpr int kPair = FNR_MLP_PAIR;                  // tiles in flight per CTA
 #ifndef FNR_MLP_FIRST_EPI
 #define FNR_MLP_FIRST_EPI 4
@@ -84,8 +109,8 @@ constexpr size_t kStageBytes = size_t(kTileM) * kMaxK0 * 2;                 // 1
 constexpr size_t kSmemStage = size_t(kPair) * kStageBytes;
 constexpr size_t kSmemRing = size_t(kSlots) * kSlotBytes;                   // weight chunks
 constexpr size_t kSmemBias = FNR_MLP_BIAS_SMEM ? size_t(kMaxBias) * 4 : 0;  // 16 KB biases (else read via L1)
-constexpr int kBars = 2 * kSlots + 5 * kPair + 1;  // full, empty; acc_full, a_ready, enc_ready, enc_free, head_ready;
-                                                   // drain
+constexpr int kBars = 3 * kSlots + 5 * kPair + 1;  // full, empty, pair_full; acc_full, a_ready, enc_ready, enc_free,
+                                                   // head_ready; drain
 constexpr size_t kSmemBars = (size_t(kBars) * 8 + 16 + 127) / 128 * 128;
 constexpr size_t kSmemBytes = kSmemA + kSmemStage + kSmemRing + kSmemBias + kSmemBars + 1024;  // + alignment slack
 static_assert(size_t(kTileM) * (kMaxHeadOut + 4) * 4 <= size_t(kTileM) * kMaxK * 2, "head staging fits an A tile");
@@ -139,26 +164,58 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// kCluster: acquire at cluster scope, for a barrier that the other CTA of the
+// pair arrives on with data of its own to order (epilogue and encoder
+// hand-offs); else the default CTA scope (weight chunks, slot releases,
+// accumulators: completions of the pair's own copies and tensor-core work).
+template <bool kCluster>
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
+    if (kCluster)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
     return ok != 0;
 }
 
+// The same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+
+// Arrive on an mbarrier of the other CTA of the pair (address from cluster_addr).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release;\n barrier.cluster.wait.acquire;" ::: "memory");
+}
+
 // Bounded wait: false when `limit` polls run out (the error word and the
-// CTA's abort flag are then set) or when another role has aborted.
+// CTA's abort flag -- and the peer CTA's, at cluster address peer_abort if
+// non-zero -- are then set) or when another role has aborted.
+template <bool kCluster>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag,
-                                          long long limit) {
+                                          long long limit, uint32_t peer_abort) {
     for (long long it = 0; it < limit; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait<kCluster>(bar, parity)) return true;
         if ((it & 1023) == 1023 && *abort_flag) return false;
     }
     atomicExch(err, 1);
     *abort_flag = 1;
+    if (peer_abort) asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer_abort), "r"(1) : "memory");
     return false;
 }
 
@@ -166,7 +223,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *er
 // (and the error word set) if it does not complete within kDrainLimit polls.
 __device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity, int *err) {
     for (long long it = 0; it < kDrainLimit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait<kCtas == 2>(bar, parity)) return true;
     atomicExch(err, 2);
     return false;
 }
@@ -217,14 +274,14 @@ __device__ __forceinline__ uint32_t instr_desc(int M, int N) {
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma." FNR_CTA_GROUP ".kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+    asm volatile("tcgen05.commit." FNR_CTA_GROUP ".mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 // 16 columns of this warp's TMEM lane quarter, without waiting (see tmem_wait).
@@ -342,25 +399,43 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kBars);
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // bars: [0, kSlots) full, [kSlots, 2 kSlots) empty, then per tile slot: acc_full, a_ready, enc_ready,
-    // enc_free, head_ready
+    // Rank in the CTA pair: rank 0 issues the MMAs for both; every shared-memory
+    // layout below is the same in both CTAs, so an address names the same
+    // object in either.
+    uint32_t rank = 0;
+    if (kCtas == 2) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const bool leader = rank == 0;
+    // bars: [0, kSlots) full, [kSlots, 2 kSlots) empty, [2 kSlots, 3 kSlots) pair_full, then per tile slot:
+    // acc_full, a_ready, enc_ready, enc_free, head_ready
     const uint32_t bar0 = smem_u32(bars);
     auto full_bar = [&](int s) { return bar0 + 8u * uint32_t(s); };
     auto empty_bar = [&](int s) { return bar0 + 8u * uint32_t(kSlots + s); };
-    auto tile_bar = [&](int which, int t) { return bar0 + 8u * uint32_t(2 * kSlots + which * kPair + t); };
-    // acc_full(t): the tile's accumulator holds a finished layer (one tcgen05.commit)
+    // pair_full(s) (rank 0): the other CTA's part of the chunk in slot s has landed
+    auto pair_full = [&](int s) { return bar0 + 8u * uint32_t(2 * kSlots + s); };
+    auto tile_bar = [&](int which, int t) { return bar0 + 8u * uint32_t(3 * kSlots + which * kPair + t); };
+    // acc_full(t): the tile's accumulator holds a finished layer (one tcgen05.commit; rank 1: one relayed arrive)
     auto acc_full = [&](int t) { return tile_bar(0, t); };
-    // a_ready(t): the accumulator has been read and the next layer's A tile written (every epilogue warp)
+    // a_ready(t) (rank 0): the accumulators have been read and the next layer's A tiles written (every epilogue
+    // warp of both CTAs)
     auto a_ready = [&](int t) { return tile_bar(1, t); };
-    // enc_ready(t): the staging buffer holds the encoded points of the tile's next pair (both encoder warps)
+    // enc_ready(t) (rank 0): the staging buffers hold the encoded points of the tile's next pair (the encoder
+    // warps of both CTAs)
     auto enc_ready = [&](int t) { return tile_bar(2, t); };
-    // enc_free(t): the layer-0 MMAs that read the staging buffer have completed (one tcgen05.commit)
+    // enc_free(t): the layer-0 MMAs that read the staging buffers have completed (commit; rank 1: relayed)
     auto enc_free = [&](int t) { return tile_bar(3, t); };
-    // head_ready(t): every epilogue warp has staged its head outputs
+    // head_ready(t): every epilogue warp of this CTA has staged its head outputs
     auto head_ready = [&](int t) { return tile_bar(4, t); };
-    // drain: the MMA issuer's last commit (every tensor-core operation of the CTA has completed)
-    const uint32_t drain_bar = bar0 + 8u * uint32_t(2 * kSlots + 5 * kPair);
+    // drain: every tensor-core operation of the pair has completed (commit; rank 1: relayed)
+    const uint32_t drain_bar = bar0 + 8u * uint32_t(3 * kSlots + 5 * kPair);
     constexpr uint32_t kATileBytes = uint32_t(kTileM) * kMaxK * 2;
+    // the same barrier in the other CTA of the pair, and arrivals that go to rank 0's copy
+    auto other = [&](uint32_t bar) { return cluster_addr(bar, rank ^ 1u); };
+    auto arrive_at_leader = [&](uint32_t bar) {
+        if (leader) mbar_arrive(bar);
+        else mbar_arrive_remote(other(bar));
+    };
+    const uint32_t peer_abort =
+        kCtas == 2 ? cluster_addr(smem_u32(const_cast<int *>(&abort_flag)), rank ^ 1u) : 0u;
 
     if (FNR_MLP_BIAS_SMEM)
         for (int i = tid; i < A.n_bias; i += kThreads) sbias[i] = A.bias[i];
@@ -368,11 +443,12 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
         for (int s = 0; s < kSlots; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
+            mbar_init(pair_full(s), 1);
         }
         for (int t = 0; t < kPair; ++t) {
             mbar_init(acc_full(t), 1);
-            mbar_init(a_ready(t), kEpiWarps);
-            mbar_init(enc_ready(t), kEncWarps);
+            mbar_init(a_ready(t), kEpiWarps * kCtas);
+            mbar_init(enc_ready(t), kEncWarps * kCtas);
             mbar_init(enc_free(t), 1);
             mbar_init(head_ready(t), kEpiWarps);
         }
@@ -380,72 +456,81 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kMmaWarp) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+    if (warp == kMmaWarp) {  // both CTAs of a pair allocate together
+        asm volatile("tcgen05.alloc." FNR_CTA_GROUP ".sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
                      "r"(kTmemCols)
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit." FNR_CTA_GROUP ".sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
+    if (kCtas == 2) cluster_sync();  // both CTAs' barriers are initialised before any remote arrive
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    // Tiles go to CTAs in groups of kPair: group r holds tiles (kPair r + t) * grid + bid, t < kPair;
-    // a tile past the end is carried as an empty one (no outputs).
-    const long long n_tiles = (A.n_points + kTileM - 1) / kTileM;
-    const long long G = gridDim.x;
-    auto pair_tile = [&](long long r, int t) { return (kPair * r + t) * G + blockIdx.x; };
-    const long long bid = blockIdx.x;
+    // MMA tiles of kSuperM points go to CTAs (pairs) in groups of kPair: group r holds tiles
+    // (kPair r + t) * grid + bid, t < kPair; a tile past the end is carried as an empty one (no outputs).
+    // CTA `rank` of a pair holds rows [rank kTileM, rank kTileM + kTileM) of each tile.
+    const long long n_tiles = (A.n_points + kSuperM - 1) / kSuperM;
+    const long long G = gridDim.x / kCtas;
+    const long long bid = blockIdx.x / kCtas;
+    auto pair_tile = [&](long long r, int t) { return (kPair * r + t) * G + bid; };
     const long long n_pairs = n_tiles > bid ? (n_tiles - bid + kPair * G - 1) / (kPair * G) : 0;
-    // a warp-wide bounded wait (lane 0 polls); false when it ran out or another role aborted
+    // bounded waits: hand-offs between the CTAs of a pair (cluster scope), and completions
+    // of copies and tensor-core work (CTA scope)
+    auto wait = [&](uint32_t bar, uint32_t parity) {
+        return mbar_wait<kCtas == 2>(bar, parity, A.err, &abort_flag, A.wait_limit, peer_abort);
+    };
+    auto wait_done = [&](uint32_t bar, uint32_t parity) {
+        return mbar_wait<false>(bar, parity, A.err, &abort_flag, A.wait_limit, peer_abort);
+    };
+    // a warp-wide bounded wait on a completion or a hand-off within the CTA (lane 0 polls); false
+    // when it ran out or another role aborted
     auto warp_wait = [&](uint32_t bar, uint32_t parity) {
         int ok = 1;
-        if (lane == 0) ok = mbar_wait(bar, parity, A.err, &abort_flag, A.wait_limit) ? 1 : 0;
+        if (lane == 0) ok = wait_done(bar, parity) ? 1 : 0;
         return __shfl_sync(0xffffffffu, ok, 0) != 0;
     };
 
     if (warp == kProducerWarp) {
         if (lane == 0) {
-            long long it = 0;
-            static_assert(kSlots == 2, "the producer tracks two ring slots");
-            long long issued0 = -1, issued1 = -1;  // per slot: the round of its last bulk copy (-1: none)
+            long long it = 0, last = -1;  // last: index of the last chunk copied
             for (long long r = 0; r < n_pairs && !abort_flag; ++r)
                 for (int li = 0; li < A.n_layers && !abort_flag; ++li)
                     for (int t = 0; t < kPair && !abort_flag; ++t) {
                         const MlpLayerDev &Ly = A.L[li];
                         const int nc = n_chunks(Ly.K);
+                        // this CTA's rows of each chunk: [rank N / kCtas, (rank + 1) N / kCtas), whole 8-row atoms
+                        const uint32_t bytes = uint32_t(Ly.N / kCtas) * uint32_t(kChunkK) * 2u;
                         for (int c = 0; c < nc; ++c, ++it) {
                             const int slot = int(it % kSlots);
                             const long long round = it / kSlots;
-                            if (round > 0 && !mbar_wait(empty_bar(slot), uint32_t((round - 1) & 1), A.err,
-                                                        &abort_flag, A.wait_limit))
-                                break;
+                            if (round > 0 && !wait_done(empty_bar(slot), uint32_t((round - 1) & 1))) break;
                             if (it == A.withhold) continue;  // test fault: this chunk never arrives
-                            const uint32_t bytes = uint32_t(Ly.N) * uint32_t(kChunkK) * 2u;
                             mbar_expect_tx(full_bar(slot), bytes);
-                            const char *src = reinterpret_cast<const char *>(Ly.w) + size_t(c) * Ly.N * kChunkK * 2;
+                            const char *src = reinterpret_cast<const char *>(Ly.w) + size_t(c) * Ly.N * kChunkK * 2 +
+                                              size_t(rank) * bytes;
                             bulk_g2s(smem_u32(ring) + uint32_t(slot) * kSlotBytes, src, bytes, full_bar(slot));
-                            if (slot == 0) issued0 = round;
-                            else issued1 = round;
+                            last = it;
                         }
                     }
             // Every copy issued has landed before the CTA's shared memory goes away
-            // (after an abort some may not have been waited for).
-            if (issued0 >= 0) mbar_drain(full_bar(0), uint32_t(issued0 & 1), A.err);
-            if (issued1 >= 0) mbar_drain(full_bar(1), uint32_t(issued1 & 1), A.err);
+            // (after an abort some may not have been waited for): the last kSlots
+            // copies, one per slot; earlier ones were consumed before their slot was reused.
+            for (long long j = last >= kSlots ? last - kSlots + 1 : 0; j <= last; ++j)
+                if (j != A.withhold) mbar_drain(full_bar(int(j % kSlots)), uint32_t((j / kSlots) & 1), A.err);
         }
     } else if (warp == kMmaWarp) {
-        if (lane == 0) {
+        if (lane == 0 && leader) {
             long long it = 0, uses = 0;  // uses: (layer, tile) steps per slot t, same count for both
             for (long long r = 0; r < n_pairs && !abort_flag; ++r)
                 for (int li = 0; li < A.n_layers && !abort_flag; ++li, ++uses)
                     for (int t = 0; t < kPair && !abort_flag; ++t) {
                         const MlpLayerDev &Ly = A.L[li];
-                        if (li == 0 && !mbar_wait(enc_ready(t), uint32_t(r & 1), A.err, &abort_flag, A.wait_limit))
-                            break;
-                        if (!mbar_wait(a_ready(t), uint32_t(uses & 1), A.err, &abort_flag, A.wait_limit)) break;
+                        if (li == 0 && !wait(enc_ready(t), uint32_t(r & 1))) break;
+                        if (!wait(a_ready(t), uint32_t(uses & 1))) break;
                         tc_fence_after();
-                        const uint32_t idesc = instr_desc(kTileM, Ly.N);
+                        const uint32_t idesc = instr_desc(kSuperM, Ly.N);
                         const uint32_t a_base =
                             li == 0 ? smem_u32(stage) + uint32_t(t) * uint32_t(kStageBytes)
                                     : smem_u32(sa) + uint32_t(t) * kATileBytes;
@@ -453,9 +538,9 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                         const int nc = n_chunks(Ly.K);
                         for (int c = 0; c < nc; ++c, ++it) {
                             const int slot = int(it % kSlots);
-                            if (!mbar_wait(full_bar(slot), uint32_t((it / kSlots) & 1), A.err, &abort_flag,
-                                           A.wait_limit))
-                                break;
+                            const uint32_t par = uint32_t((it / kSlots) & 1);
+                            if (!wait_done(full_bar(slot), par)) break;
+                            if (kCtas == 2 && !wait_done(pair_full(slot), par)) break;
                             tc_fence_after();
 #pragma unroll
                             for (int s = 0; s < kChunkK / 16; ++s) {
@@ -466,33 +551,56 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                                 umma_bf16(d_tmem, ad, bd, idesc, (c > 0 || s > 0) ? 1u : 0u);
                             }
                             umma_commit(empty_bar(slot));
+                            if (kCtas == 2) umma_commit(other(empty_bar(slot)));
                         }
                         if (abort_flag) break;
-                        if (li == 0) umma_commit(enc_free(t));  // the staging buffer may be refilled
+                        if (li == 0) {  // the staging buffers may be refilled
+                            umma_commit(enc_free(t));
+                            if (kCtas == 2) umma_commit(other(enc_free(t)));
+                        }
                         umma_commit(acc_full(t));
+                        if (kCtas == 2) umma_commit(other(acc_full(t)));
                     }
             // every tensor-core operation issued (and every commit before this one) has
-            // completed before the tensor memory is freed and the CTA leaves
+            // completed before the tensor memory is freed and the CTAs leave
             umma_commit(drain_bar);
+            if (kCtas == 2) umma_commit(other(drain_bar));
+            mbar_drain(drain_bar, 0u, A.err);
+        } else if (lane == 0) {
+            // rank 1: tell rank 0 when each of this CTA's chunk parts has landed, in chunk order
+            long long it = 0;
+            for (long long r = 0; r < n_pairs && !abort_flag; ++r)
+                for (int li = 0; li < A.n_layers && !abort_flag; ++li)
+                    for (int t = 0; t < kPair && !abort_flag; ++t) {
+                        const int nc = n_chunks(A.L[li].K);
+                        for (int c = 0; c < nc; ++c, ++it) {
+                            const int slot = int(it % kSlots);
+                            if (!wait_done(full_bar(slot), uint32_t((it / kSlots) & 1))) break;
+                            mbar_arrive_remote(other(pair_full(slot)));
+                        }
+                    }
+            // rank 0's MMAs read this CTA's shared memory and write its tensor memory:
+            // they have completed before either is released
             mbar_drain(drain_bar, 0u, A.err);
         }
     } else if (warp >= kEncWarp0 && warp < kEncWarp0 + kEncWarps) {
-        // encoders: rows (warp - kEncWarp0) * 32 + lane + 32 kEncWarps i of each tile
+        // encoders: rows (warp - kEncWarp0) * 32 + lane + 32 kEncWarps i of this CTA's part of each tile
         const int e = warp - kEncWarp0;
         for (long long r = 0; r < n_pairs && !abort_flag; ++r) {
             bool ok = true;
             for (int t = 0; t < kPair && ok; ++t) {
-                // pair r - 1's layer-0 MMAs of this slot have read the buffer
+                // pair r - 1's layer-0 MMAs of this slot have read the buffers
                 if (r > 0 && !(ok = warp_wait(enc_free(t), uint32_t((r - 1) & 1)))) break;
                 const long long tile = pair_tile(r, t);
                 char *st = stage + size_t(t) * kStageBytes;
                 for (int row = e * 32 + lane; row < kTileM; row += 32 * kEncWarps) {
-                    const long long p = tile < n_tiles ? tile * kTileM + row : A.n_points;  // past the end: zeros
+                    const long long p =
+                        tile < n_tiles ? tile * kSuperM + rank * kTileM + row : A.n_points;  // past the end: zeros
                     encode_point(A, p, row, st);
                 }
                 fence_proxy_async();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(enc_ready(t));
+                if (lane == 0) arrive_at_leader(enc_ready(t));
             }
             if (!ok) break;
         }
@@ -506,7 +614,7 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
         if (n_pairs > 0)
             for (int t = 0; t < kPair; ++t) {
                 __syncwarp();
-                if (lane == 0) mbar_arrive(a_ready(t));
+                if (lane == 0) arrive_at_leader(a_ready(t));
             }
         for (long long r = 0; r < n_pairs && !stop; ++r) {
             for (int li = 0; li < A.n_layers && !stop; ++li, ++uses) {
@@ -559,7 +667,7 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                         tc_fence_before();
                         fence_proxy_async();
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(a_ready(t));
+                        if (lane == 0) arrive_at_leader(a_ready(t));
                         continue;
                     }
                     // head: stage out_c + bias (c < n_out) as fp32 rows of head_stride floats in the A tile,
@@ -587,11 +695,13 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                         stop = true;
                         break;
                     }
-                    // the tile's outputs are contiguous ranges of the cache (or of out): element e of the
-                    // range belongs to row e / n and output e % n
+                    // this CTA's outputs of the tile are contiguous ranges of the cache (or of out):
+                    // element e of the range belongs to row e / n and output e % n
                     const long long tile = pair_tile(r, t);
-                    const long long p0 = tile * kTileM;
-                    const int nv = tile < n_tiles ? int(A.n_points - p0 < kTileM ? A.n_points - p0 : kTileM) : 0;
+                    const long long p0 = tile * kSuperM + rank * kTileM;
+                    const int nv = tile < n_tiles && p0 < A.n_points
+                                       ? int(A.n_points - p0 < kTileM ? A.n_points - p0 : kTileM)
+                                       : 0;
                     constexpr int kEpiThreads = 32 * kEpiWarps;
                     if (A.mode == 0) {
                         for (int i = te; i < nv; i += kEpiThreads) {
@@ -628,15 +738,18 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                     // the staged rows have been read: the next pair's layer 0 may use the accumulator
                     // and its epilogue may overwrite the A tile
                     __syncwarp();
-                    if (r + 1 < n_pairs && lane == 0) mbar_arrive(a_ready(t));
+                    if (r + 1 < n_pairs && lane == 0) arrive_at_leader(a_ready(t));
                 }
             }
         }
     }
     __syncthreads();
+    // no arrive or MMA of one CTA of the pair targets the other after this point
+    if (kCtas == 2) cluster_sync();
     if (warp == kMmaWarp) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.dealloc." FNR_CTA_GROUP ".sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
     }
 }
 
@@ -739,10 +852,31 @@ fnr_status mlp_launch(const fnr_mlp *m, MlpArgs &A, int num_sms, cudaStream_t s)
     if ((e = cudaFuncSetAttribute(mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes))) !=
         cudaSuccess)
         return cuda_fail(e, "MLP smem attribute");
-    const long long tiles = (A.n_points + kTileM - 1) / kTileM;
-    const int grid = int(tiles < num_sms ? tiles : num_sms);
-    mlp_kernel<<<grid, kThreads, kSmemBytes, s>>>(A);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "MLP launch");
+    const long long tiles = (A.n_points + kSuperM - 1) / kSuperM;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(kCtas);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = kCtas > 1 ? 1 : 0;
+    // one CTA (pair) per SM (pair) that can be resident at once
+    int units = num_sms / kCtas;
+    if (kCtas > 1) {
+        cfg.gridDim = dim3(unsigned(num_sms / kCtas * kCtas));
+        int clusters = 0;
+        if ((e = cudaOccupancyMaxActiveClusters(&clusters, mlp_kernel, &cfg)) != cudaSuccess)
+            return cuda_fail(e, "MLP cluster occupancy");
+        if (clusters < 1) return fail(FNR_ERR_UNSUPPORTED, "MLP kernel: no SM pair can hold a CTA pair");
+        units = clusters;
+    }
+    const int grid = int(tiles < units ? tiles : units) * kCtas;
+    cfg.gridDim = dim3(unsigned(grid));
+    if ((e = cudaLaunchKernelEx(&cfg, mlp_kernel, A)) != cudaSuccess) return cuda_fail(e, "MLP launch");
     int herr = 0;
     if ((e = cudaMemcpyAsync(&herr, ebuf.p, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
