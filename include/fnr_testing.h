@@ -1,13 +1,14 @@
 /*
- * fnr_testing.h -- failure-injection hooks of libfnr, for tests only.
+ * fnr_testing.h -- test hooks of libfnr, for tests only.
  *
- * The paper has no counterpart to these calls. They let a test make the
+ * The paper has no counterpart to these calls. Two of them let a test make the
  * library's error paths run without faulting a GPU: a device allocation that
  * fails, and a bounded wait inside the tensor-core cache-build kernel that runs
- * out. Production code never calls them; with no hook armed the library
- * behaves exactly as without them. Hooks are process-wide and not
- * thread-safe against concurrent builds: arm one, run the call under test,
- * and check its status.
+ * out. The third selects an alternative form of that kernel so that a test can
+ * check it against the default one. Production code never calls them; with no
+ * hook armed the library behaves exactly as without them. Hooks are
+ * process-wide and not thread-safe against concurrent builds: arm one, run the
+ * call under test, and check its status.
  */
 #ifndef FNR_TESTING_H
 #define FNR_TESTING_H
@@ -36,6 +37,15 @@ FNR_API fnr_status fnr_testing_fail_allocations(int32_t skip, int32_t count);
  * hook disarms itself after one launch. Errors: INVALID_ARG for
  * wait_limit < 1. */
 FNR_API fnr_status fnr_testing_mlp_fault(int64_t wait_limit, int64_t withhold_chunk);
+
+/* Selects the form of the tensor-core cache-build kernel for the builds that
+ * follow (fnr_build_cache with FNR_SRC_MLP, fnr_render_mlp), until called
+ * again: on != 0 the CTA-pair form -- clusters of two CTAs on an SM pair, M =
+ * 256 MMAs issued for both (tcgen05 cta_group::2), each SM holding half of every
+ * weight chunk; on = 0 (the default) the single-CTA form, M = 128 per SM. Both
+ * compute the same products in the same order: their caches are bit-identical.
+ * The pair form measured slower on the 512^3 build. Never fails. */
+FNR_API fnr_status fnr_testing_mlp_cta_pair(int32_t on);
 
 #ifdef __cplusplus
 }

@@ -143,6 +143,7 @@ SIGNATURES = {
                             _P, _P, _P], ctypes.c_int32),
     "fnr_testing_fail_allocations": ([ctypes.c_int32, ctypes.c_int32], ctypes.c_int32),
     "fnr_testing_mlp_fault": ([ctypes.c_int64, ctypes.c_int64], ctypes.c_int32),
+    "fnr_testing_mlp_cta_pair": ([ctypes.c_int32], ctypes.c_int32),
 }
 
 _lib = None
@@ -405,3 +406,8 @@ def fnr_testing_mlp_fault(wait_limit: int, withhold_chunk: int = -1) -> None:
     """The next tensor-core build launch gives up its waits after wait_limit polls and, if withhold_chunk >= 0,
     each CTA's producer withholds that weight chunk; the call then returns FNR_ERR_DEVICE."""
     check(lib().fnr_testing_mlp_fault(int(wait_limit), int(withhold_chunk)))
+
+
+def fnr_testing_mlp_cta_pair(on: bool) -> None:
+    """Builds that follow use the CTA-pair form of the tensor-core kernel (on) or the default single-CTA form."""
+    check(lib().fnr_testing_mlp_cta_pair(1 if on else 0))

@@ -111,6 +111,9 @@ cudaError_t dev_malloc(T **p, size_t bytes) {
 // The armed cache-build fault (fnr_testing_mlp_fault), taken once: leaves the
 // arguments unchanged when none is armed.
 void take_mlp_fault(long long *wait_limit, long long *withhold);
+// Whether cache builds use the CTA-pair form of the tensor-core kernel
+// (fnr_testing_mlp_cta_pair); the single-CTA form otherwise.
+bool mlp_cta_pair();
 int rec_stride_bytes(int prec, int D);
 size_t elem_bytes(int prec);
 

@@ -3,18 +3,20 @@
 // Section 3.2 Eqs. 3-4 and Section 4: F_pos and F_dir are ReLU MLPs on
 // positionally encoded inputs).
 //
-// A pair of CTAs on two SMs (a cluster of two) walks tiles of 256 grid points,
-// each CTA holding 128 of them; rank 0 issues M = 256 MMAs for the pair
-// (tcgen05.mma.cta_group::2) that read each CTA's A rows and each CTA's half of
-// the weight chunk from that CTA's own shared memory and accumulate into each
-// CTA's own tensor memory. Each SM therefore streams half of every weight chunk
-// per MMA tile. Warp roles, in both CTAs:
-//   producer (warp 0): streams this CTA's half of every layer's bf16 weights,
-//     pre-arranged in 64-column K chunks of the K-major 128-byte swizzled
-//     operand layout, through a 4-slot shared-memory ring by bulk async copy
-//     (cp.async.bulk, completion on the slot's "full" mbarrier), running ahead
-//     across layers and tiles; rank 0's producer passes each slot's release on
-//     to rank 1;
+// The kernel has two forms (template parameter CTAS). The default, CTAS = 1:
+// one CTA per SM walks tiles of 128 grid points. CTAS = 2: a cluster of two
+// CTAs on an SM pair walks tiles of 256 points, 128 per CTA; rank 0 issues
+// M = 256 MMAs for both (tcgen05.mma.cta_group::2), which read each CTA's A
+// rows and each CTA's half of the weight chunk from that CTA's own shared
+// memory and accumulate into each CTA's own tensor memory, so each SM streams
+// half of every chunk. Warp roles, in every CTA:
+//   producer (warp 0): streams every layer's bf16 weights (this CTA's half of
+//     each chunk in the pair form), pre-arranged in 64-column K chunks of the
+//     K-major 128-byte swizzled operand layout, through a shared-memory ring by
+//     bulk async copy (cp.async.bulk, completion on the slot's "full"
+//     mbarrier), running ahead across layers and tiles. The single-CTA ring has
+//     2 slots of 32 KB, loaded once per tile; the pair form's has 4 slots of
+//     16 KB -- a whole layer -- loaded once per layer for both tiles in flight;
 //   two tiles are in flight: each has its own A tile (same swizzled layout)
 //     and its own tensor-memory accumulator, so one tile's epilogue runs while
 //     the other's MMAs do;
@@ -22,12 +24,12 @@
 //     pi x), rounded to bf16) into the tile's layer-0 staging buffer one tile
 //     pair ahead, as soon as the MMAs that read the buffer's previous contents
 //     have completed, so encoding never waits between tiles;
-//   MMA issuer (warp 1, one lane of rank 0): waits for both CTAs' layer inputs
-//     and chunk halves, issues tcgen05.mma (M=256, N=layer width, K=16 steps,
-//     bf16 x bf16 -> fp32 in tensor memory; layer 0 reads the staging
-//     buffers), releases each slot with tcgen05.commit on its "empty" mbarrier
-//     and signals the finished accumulators with one more commit; in rank 1
-//     the same lane tells rank 0 when each chunk half has landed;
+//   MMA issuer (warp 1, one lane; rank 0 in the pair form): waits for the layer
+//     input and each chunk, issues tcgen05.mma (K=16 steps, bf16 x bf16 -> fp32
+//     in tensor memory; layer 0 reads the staging buffer), releases each slot
+//     with tcgen05.commit on its "empty" mbarrier and signals the finished
+//     accumulator with one more commit; in rank 1 of a pair the same lane tells
+//     rank 0 when each chunk half has landed;
 //   epilogue (warps 4-19, four per 32-lane quarter of tensor memory): per
 //     hidden layer read the accumulator (tcgen05.ld), add the bias, apply
 //     ReLU, round to bf16 and write the next layer's A tile; after the head,
@@ -35,16 +37,18 @@
 //     tile's sigma = ReLU(out_0), (u, v, w) = out_1..3D (F_pos) or beta =
 //     out_0..D-1 (F_dir) -- contiguous ranges of the cache -- with coalesced
 //     stores by all sixteen warps.
-// Rank 0 issues each tcgen05.commit twice, on its own copy of the barrier and,
-// through the barrier's cluster address, on rank 1's; rank 1's threads arrive
-// on rank 0's barriers with remote mbarrier arrives, and rank 1 reports each
-// landed chunk half the same way. The next layer's weights load while the
-// epilogue runs. Every mbarrier wait is bounded; a wait that runs
-// out sets the error word and both CTAs' abort flags, every role leaves its
-// loop, each producer waits (bounded) for the copies it has in flight, the
-// MMA issuer for its tensor-core operations (rank 1 for the same commit), and
-// the tensor memory is freed. Built with FNR_MLP_CTAS=1 the kernel is the
-// single-CTA form: M = 128 MMAs, whole chunks through a 2-slot ring.
+// In the pair form rank 0 issues each tcgen05.commit twice, on its own copy of
+// the barrier and, through the barrier's cluster address, on rank 1's; rank 1's
+// threads arrive on rank 0's barriers with remote mbarrier arrives. The next
+// layer's weights load while the epilogue runs. Every mbarrier wait is bounded;
+// a wait that runs out sets the error word and the abort flags of the CTA (and
+// of its pair), every role leaves its loop, each producer waits (bounded) for
+// the copies it has in flight, the MMA issuer for its tensor-core operations
+// (rank 1 for the same commit), and the tensor memory is freed. Both forms
+// compute every product in the same order; the pair form measured slower (its
+// hand-offs between the two SMs lengthen the refill and epilogue chains), so
+// the single-CTA form is the default and the pair form is chosen only through
+// the test hook fnr_testing_mlp_cta_pair.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -63,30 +67,12 @@ constexpr int kTileM = 128;
 constexpr int kMaxK = 256;
 constexpr int kMaxN = 256;
 constexpr int kChunkK = 64;                          // K columns per weight chunk: one 128-byte swizzle row
-#ifndef FNR_MLP_CTAS
-#define FNR_MLP_CTAS 1
-#endif
-// CTAs per MMA: 2 = a cluster of two CTAs on an SM pair issuing M = 256 MMAs
-// (cta_group::2), each CTA holding 128 rows of A and half of every weight chunk.
-constexpr int kCtas = FNR_MLP_CTAS;
-static_assert(kCtas == 1 || kCtas == 2, "CTAs per MMA");
-#if FNR_MLP_CTAS == 2
-#define FNR_CTA_GROUP "cta_group::2"
-#else
-#define FNR_CTA_GROUP "cta_group::1"
-#endif
-constexpr int kSuperM = kTileM * kCtas;              // points per MMA tile
-#ifndef FNR_MLP_SLOTS
-#define FNR_MLP_SLOTS (2 * FNR_MLP_CTAS)
-#endif
 #ifndef FNR_MLP_PAIR
 #define FNR_MLP_PAIR 2
 #endif
 #ifndef FNR_MLP_BIAS_SMEM
 #define FNR_MLP_BIAS_SMEM 0
 #endif
-constexpr int kSlots = FNR_MLP_SLOTS;                // ring slots
-constexpr int kSlotBytes = kMaxN / kCtas * kChunkK * 2;  // this CTA's rows of one weight chunk
 constexpr int kPair = FNR_MLP_PAIR;                  // tiles in flight per CTA
 #ifndef FNR_MLP_FIRST_EPI
 #define FNR_MLP_FIRST_EPI 4
@@ -107,14 +93,30 @@ constexpr uint32_t kTmemCols = 256 * kPair;                                // on
 constexpr size_t kSmemA = size_t(kPair) * kTileM * kMaxK * 2;               // 64 KB activations per tile
 constexpr size_t kStageBytes = size_t(kTileM) * kMaxK0 * 2;                 // 16 KB layer-0 input per tile
 constexpr size_t kSmemStage = size_t(kPair) * kStageBytes;
-constexpr size_t kSmemRing = size_t(kSlots) * kSlotBytes;                   // weight chunks
 constexpr size_t kSmemBias = FNR_MLP_BIAS_SMEM ? size_t(kMaxBias) * 4 : 0;  // 16 KB biases (else read via L1)
-constexpr int kBars = 3 * kSlots + 5 * kPair + 1;  // full, empty, pair_full; acc_full, a_ready, enc_ready, enc_free,
-                                                   // head_ready; drain
-constexpr size_t kSmemBars = (size_t(kBars) * 8 + 16 + 127) / 128 * 128;
-constexpr size_t kSmemBytes = kSmemA + kSmemStage + kSmemRing + kSmemBias + kSmemBars + 1024;  // + alignment slack
 static_assert(size_t(kTileM) * (kMaxHeadOut + 4) * 4 <= size_t(kTileM) * kMaxK * 2, "head staging fits an A tile");
-static_assert(kSmemBytes <= 232448, "shared memory per CTA");
+
+// The two forms of the kernel. CTAS = 1: one CTA per SM issues M = 128 MMAs
+// and streams whole 64-column weight chunks through a 2-slot ring. CTAS = 2:
+// a cluster of two CTAs on an SM pair; rank 0 issues M = 256 MMAs for both
+// (tcgen05 cta_group::2), each CTA holds 128 rows of A and half of every weight
+// chunk, and the 4-slot ring holds a whole layer's chunk halves, which both
+// tiles in flight read from one load.
+template <int CTAS>
+struct Form {
+    static_assert(CTAS == 1 || CTAS == 2, "CTAs per MMA");
+    static constexpr bool kShare = CTAS == 2;                       // a layer's chunks serve both tiles
+    static constexpr int kSuperM = kTileM * CTAS;                   // points per MMA tile
+    static constexpr int kSlots = 2 * CTAS;                         // ring slots
+    static constexpr int kSlotBytes = kMaxN / CTAS * kChunkK * 2;   // this CTA's rows of one weight chunk
+    static constexpr size_t kSmemRing = size_t(kSlots) * kSlotBytes;
+    // full, empty, pair_full; per tile slot acc_full, a_ready, enc_ready, enc_free, head_ready; drain
+    static constexpr int kBars = 3 * kSlots + 5 * kPair + 1;
+    static constexpr size_t kSmemBars = (size_t(kBars) * 8 + 16 + 127) / 128 * 128;
+    static constexpr size_t kSmemBytes = kSmemA + kSmemStage + kSmemRing + kSmemBias + kSmemBars + 1024;  // + slack
+    static_assert(kSmemBytes <= 232448, "shared memory per CTA");
+    static_assert(!kShare || kMaxK / kChunkK <= kSlots, "a layer's chunks fit the ring");
+};
 constexpr long long kWaitLimit = 1LL << 22;                                 // try_wait polls before giving up
 constexpr long long kDrainLimit = 1LL << 22;                                // polls for in-flight work at exit
 
@@ -221,9 +223,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *er
 
 // Bounded wait at exit for work this CTA has in flight, abort or not; false
 // (and the error word set) if it does not complete within kDrainLimit polls.
+template <bool kCluster>
 __device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity, int *err) {
     for (long long it = 0; it < kDrainLimit; ++it)
-        if (mbar_try_wait<kCtas == 2>(bar, parity)) return true;
+        if (mbar_try_wait<kCluster>(bar, parity)) return true;
     atomicExch(err, 2);
     return false;
 }
@@ -271,17 +274,54 @@ __device__ __forceinline__ uint32_t instr_desc(int M, int N) {
     return d;
 }
 
+template <int CTAS>
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma." FNR_CTA_GROUP ".kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
+    if constexpr (CTAS == 2)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::
+                "r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::
+                "r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
 }
 
+// Arrive on the mbarrier at shared::cluster address `bar` when every tcgen05
+// operation this thread has issued so far has completed.
+template <int CTAS>
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit." FNR_CTA_GROUP ".mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+    if constexpr (CTAS == 2)
+        asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+    else
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Tensor-memory allocation of `cols` columns by one whole warp (in both CTAs of a pair,
+// together), its address written to shared memory at `slot`; and its release.
+template <int CTAS>
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t cols) {
+    if constexpr (CTAS == 2) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+}
+
+template <int CTAS>
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t cols) {
+    if constexpr (CTAS == 2)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+    else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
 }
 
 // 16 columns of this warp's TMEM lane quarter, without waiting (see tmem_wait).
@@ -387,7 +427,13 @@ __device__ __forceinline__ void encode_point(const MlpArgs &A, long long p, int 
 
 __device__ __forceinline__ int n_chunks(int K) { return K / kChunkK; }  // K is padded to a multiple of 64
 
+template <int CTAS>
 __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
+    using F = Form<CTAS>;
+    constexpr int kCtas = CTAS, kSlots = F::kSlots, kSlotBytes = F::kSlotBytes, kBars = F::kBars;
+    constexpr long long kSuperM = F::kSuperM;
+    constexpr bool kShare = F::kShare;
+    constexpr size_t kSmemRing = F::kSmemRing;
     extern __shared__ __align__(1024) char smem_raw[];
     // the swizzled operand tiles start on 1024-byte boundaries
     char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -456,13 +502,7 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kMmaWarp) {  // both CTAs of a pair allocate together
-        asm volatile("tcgen05.alloc." FNR_CTA_GROUP ".sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tmem_slot)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit." FNR_CTA_GROUP ".sync.aligned;" ::: "memory");
-    }
+    if (warp == kMmaWarp) tmem_alloc<CTAS>(smem_u32(tmem_slot), kTmemCols);  // both CTAs of a pair together
     tc_fence_before();
     __syncthreads();
     if (kCtas == 2) cluster_sync();  // both CTAs' barriers are initialised before any remote arrive
@@ -497,7 +537,7 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
             long long it = 0, last = -1;  // last: index of the last chunk copied
             for (long long r = 0; r < n_pairs && !abort_flag; ++r)
                 for (int li = 0; li < A.n_layers && !abort_flag; ++li)
-                    for (int t = 0; t < kPair && !abort_flag; ++t) {
+                    for (int t = 0; t < (kShare ? 1 : kPair) && !abort_flag; ++t) {  // once per tile, or once
                         const MlpLayerDev &Ly = A.L[li];
                         const int nc = n_chunks(Ly.K);
                         // this CTA's rows of each chunk: [rank N / kCtas, (rank + 1) N / kCtas), whole 8-row atoms
@@ -518,7 +558,7 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
             // (after an abort some may not have been waited for): the last kSlots
             // copies, one per slot; earlier ones were consumed before their slot was reused.
             for (long long j = last >= kSlots ? last - kSlots + 1 : 0; j <= last; ++j)
-                if (j != A.withhold) mbar_drain(full_bar(int(j % kSlots)), uint32_t((j / kSlots) & 1), A.err);
+                if (j != A.withhold) mbar_drain<kCtas == 2>(full_bar(int(j % kSlots)), uint32_t((j / kSlots) & 1), A.err);
         }
     } else if (warp == kMmaWarp) {
         if (lane == 0 && leader) {
@@ -527,6 +567,7 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                 for (int li = 0; li < A.n_layers && !abort_flag; ++li, ++uses)
                     for (int t = 0; t < kPair && !abort_flag; ++t) {
                         const MlpLayerDev &Ly = A.L[li];
+                        if (kShare && t > 0) it -= n_chunks(Ly.K);  // the layer's chunks again, still in the ring
                         if (li == 0 && !wait(enc_ready(t), uint32_t(r & 1))) break;
                         if (!wait(a_ready(t), uint32_t(uses & 1))) break;
                         tc_fence_after();
@@ -539,8 +580,9 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                         for (int c = 0; c < nc; ++c, ++it) {
                             const int slot = int(it % kSlots);
                             const uint32_t par = uint32_t((it / kSlots) & 1);
-                            if (!wait_done(full_bar(slot), par)) break;
-                            if (kCtas == 2 && !wait_done(pair_full(slot), par)) break;
+                            const bool first = !kShare || t == 0;  // the chunk's first use: wait for it to land
+                            if (first && !wait_done(full_bar(slot), par)) break;
+                            if (kCtas == 2 && first && !wait_done(pair_full(slot), par)) break;
                             tc_fence_after();
 #pragma unroll
                             for (int s = 0; s < kChunkK / 16; ++s) {
@@ -548,30 +590,32 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                                                                     uint32_t(s) * 32u);
                                 const uint64_t bd =
                                     smem_desc_sw128(smem_u32(ring) + uint32_t(slot) * kSlotBytes + uint32_t(s) * 32u);
-                                umma_bf16(d_tmem, ad, bd, idesc, (c > 0 || s > 0) ? 1u : 0u);
+                                umma_bf16<CTAS>(d_tmem, ad, bd, idesc, (c > 0 || s > 0) ? 1u : 0u);
                             }
-                            umma_commit(empty_bar(slot));
-                            if (kCtas == 2) umma_commit(other(empty_bar(slot)));
+                            if (!kShare || t == kPair - 1) {  // its last use: the slot may be refilled
+                                umma_commit<CTAS>(empty_bar(slot));
+                                if (kCtas == 2) umma_commit<CTAS>(other(empty_bar(slot)));
+                            }
                         }
                         if (abort_flag) break;
                         if (li == 0) {  // the staging buffers may be refilled
-                            umma_commit(enc_free(t));
-                            if (kCtas == 2) umma_commit(other(enc_free(t)));
+                            umma_commit<CTAS>(enc_free(t));
+                            if (kCtas == 2) umma_commit<CTAS>(other(enc_free(t)));
                         }
-                        umma_commit(acc_full(t));
-                        if (kCtas == 2) umma_commit(other(acc_full(t)));
+                        umma_commit<CTAS>(acc_full(t));
+                        if (kCtas == 2) umma_commit<CTAS>(other(acc_full(t)));
                     }
             // every tensor-core operation issued (and every commit before this one) has
             // completed before the tensor memory is freed and the CTAs leave
-            umma_commit(drain_bar);
-            if (kCtas == 2) umma_commit(other(drain_bar));
-            mbar_drain(drain_bar, 0u, A.err);
+            umma_commit<CTAS>(drain_bar);
+            if (kCtas == 2) umma_commit<CTAS>(other(drain_bar));
+            mbar_drain<kCtas == 2>(drain_bar, 0u, A.err);
         } else if (lane == 0) {
             // rank 1: tell rank 0 when each of this CTA's chunk parts has landed, in chunk order
             long long it = 0;
             for (long long r = 0; r < n_pairs && !abort_flag; ++r)
                 for (int li = 0; li < A.n_layers && !abort_flag; ++li)
-                    for (int t = 0; t < kPair && !abort_flag; ++t) {
+                    for (int t = 0; t < (kShare ? 1 : kPair) && !abort_flag; ++t) {
                         const int nc = n_chunks(A.L[li].K);
                         for (int c = 0; c < nc; ++c, ++it) {
                             const int slot = int(it % kSlots);
@@ -581,7 +625,7 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
                     }
             // rank 0's MMAs read this CTA's shared memory and write its tensor memory:
             // they have completed before either is released
-            mbar_drain(drain_bar, 0u, A.err);
+            mbar_drain<kCtas == 2>(drain_bar, 0u, A.err);
         }
     } else if (warp >= kEncWarp0 && warp < kEncWarp0 + kEncWarps) {
         // encoders: rows (warp - kEncWarp0) * 32 + lane + 32 kEncWarps i of this CTA's part of each tile
@@ -748,8 +792,7 @@ __global__ void FNR_MLP_KATTR mlp_kernel(const __grid_constant__ MlpArgs A) {
     if (kCtas == 2) cluster_sync();
     if (warp == kMmaWarp) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc." FNR_CTA_GROUP ".sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
-                     : "memory");
+        tmem_free<CTAS>(tmem, kTmemCols);
     }
 }
 
@@ -802,6 +845,42 @@ fnr_status check_mlp(const fnr_mlp *m, int n_out_min, const char *name) {
 
 namespace {
 
+// Launch one form of the kernel: one CTA (pair) per SM (pair) that can be
+// resident at once, at most one per MMA tile.
+template <int CTAS>
+fnr_status launch_form(const MlpArgs &A, int num_sms, cudaStream_t s) {
+    using F = Form<CTAS>;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(mlp_kernel<CTAS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(F::kSmemBytes))) != cudaSuccess)
+        return cuda_fail(e, "MLP smem attribute");
+    const long long tiles = (A.n_points + F::kSuperM - 1) / F::kSuperM;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(CTAS);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = F::kSmemBytes;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = CTAS > 1 ? 1 : 0;
+    int units = num_sms;
+    if (CTAS > 1) {
+        cfg.gridDim = dim3(unsigned(num_sms / CTAS * CTAS));
+        int clusters = 0;
+        if ((e = cudaOccupancyMaxActiveClusters(&clusters, mlp_kernel<CTAS>, &cfg)) != cudaSuccess)
+            return cuda_fail(e, "MLP cluster occupancy");
+        if (clusters < 1) return fail(FNR_ERR_UNSUPPORTED, "MLP kernel: no SM pair can hold a CTA pair");
+        units = clusters;
+    }
+    const int grid = int(tiles < units ? tiles : units) * CTAS;
+    cfg.gridDim = dim3(unsigned(grid));
+    if ((e = cudaLaunchKernelEx(&cfg, mlp_kernel<CTAS>, A)) != cudaSuccess) return cuda_fail(e, "MLP launch");
+    return FNR_OK;
+}
+
 // Lay out the weights and biases of m, fill the layer table of A, launch the
 // kernel on the mode-specific arguments already in A, and wait for it.
 fnr_status mlp_launch(const fnr_mlp *m, MlpArgs &A, int num_sms, cudaStream_t s) {
@@ -849,34 +928,8 @@ fnr_status mlp_launch(const fnr_mlp *m, MlpArgs &A, int num_sms, cudaStream_t s)
     if (A.n_out < 1 || A.n_out > kMaxHeadOut || A.n_out > A.L[m->n_layers - 1].N)
         return fail(FNR_ERR_UNSUPPORTED, "MLP kernel: %d outputs per point (at most %d)", A.n_out, kMaxHeadOut);
     if (A.n_points <= 0) return FNR_OK;
-    if ((e = cudaFuncSetAttribute(mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes))) !=
-        cudaSuccess)
-        return cuda_fail(e, "MLP smem attribute");
-    const long long tiles = (A.n_points + kSuperM - 1) / kSuperM;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = unsigned(kCtas);
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = kSmemBytes;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = kCtas > 1 ? 1 : 0;
-    // one CTA (pair) per SM (pair) that can be resident at once
-    int units = num_sms / kCtas;
-    if (kCtas > 1) {
-        cfg.gridDim = dim3(unsigned(num_sms / kCtas * kCtas));
-        int clusters = 0;
-        if ((e = cudaOccupancyMaxActiveClusters(&clusters, mlp_kernel, &cfg)) != cudaSuccess)
-            return cuda_fail(e, "MLP cluster occupancy");
-        if (clusters < 1) return fail(FNR_ERR_UNSUPPORTED, "MLP kernel: no SM pair can hold a CTA pair");
-        units = clusters;
-    }
-    const int grid = int(tiles < units ? tiles : units) * kCtas;
-    cfg.gridDim = dim3(unsigned(grid));
-    if ((e = cudaLaunchKernelEx(&cfg, mlp_kernel, A)) != cudaSuccess) return cuda_fail(e, "MLP launch");
+    const fnr_status st = mlp_cta_pair() ? launch_form<2>(A, num_sms, s) : launch_form<1>(A, num_sms, s);
+    if (st != FNR_OK) return st;
     int herr = 0;
     if ((e = cudaMemcpyAsync(&herr, ebuf.p, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)

@@ -1,5 +1,6 @@
-// testing.cu -- failure-injection hooks (fnr_testing.h) and the one device
-// allocation helper every library allocation goes through.
+// testing.cu -- test hooks (fnr_testing.h): failure injection and the choice
+// of the cache-build kernel's form; and the one device allocation helper every
+// library allocation goes through.
 #include <atomic>
 
 #include "fnr_internal.h"
@@ -13,7 +14,10 @@ void clear_error();
 namespace {
 std::atomic<int> g_alloc_skip{0}, g_alloc_fail{0};
 std::atomic<long long> g_mlp_wait_limit{0}, g_mlp_withhold{-1};
+std::atomic<int> g_mlp_cta_pair{0};
 }  // namespace
+
+bool mlp_cta_pair() { return g_mlp_cta_pair.load() != 0; }
 
 cudaError_t dev_malloc(void **p, size_t bytes) {
     if (g_alloc_fail.load() > 0) {
@@ -55,5 +59,11 @@ extern "C" fnr_status fnr_testing_mlp_fault(int64_t wait_limit, int64_t withhold
     if (wait_limit < 1) return fail(FNR_ERR_INVALID_ARG, "wait_limit must be >= 1");
     g_mlp_withhold.store(withhold_chunk);
     g_mlp_wait_limit.store(wait_limit);
+    return FNR_OK;
+}
+
+extern "C" fnr_status fnr_testing_mlp_cta_pair(int32_t on) {
+    clear_error();
+    g_mlp_cta_pair.store(on != 0 ? 1 : 0);
     return FNR_OK;
 }

@@ -122,9 +122,10 @@ def test_binding_constants_match_header(fnr):
 
 
 def test_testing_hooks_validate_arguments(fnr):
-    """The failure-injection hooks (fnr_testing.h) check their arguments and arm / disarm without touching
-    the device."""
+    """The test hooks (fnr_testing.h) check their arguments and arm / disarm without touching the device."""
     L = fnr.lib()
+    assert L.fnr_testing_mlp_cta_pair(1) == fnr.FNR_OK
+    assert L.fnr_testing_mlp_cta_pair(0) == fnr.FNR_OK  # back to the single-CTA form
     assert L.fnr_testing_fail_allocations(-1, 1) == fnr.FNR_ERR_INVALID_ARG
     assert L.fnr_testing_fail_allocations(0, -1) == fnr.FNR_ERR_INVALID_ARG
     assert L.fnr_testing_mlp_fault(0, 3) == fnr.FNR_ERR_INVALID_ARG

@@ -53,8 +53,20 @@ def cache_bytes(fnr, cache, k, D, l):
             grab(lay.beta_dev, l * l * D * 4))
 
 
+@pytest.mark.parametrize("pair", [False, True])
 @pytest.mark.parametrize("withhold", [0, 3, 11])
-def test_build_wait_runs_out_and_recovers(fnr, withhold):
+def test_build_wait_runs_out_and_recovers(fnr, withhold, pair):
+    """Single-CTA and CTA-pair forms of the build kernel: in the pair form both CTAs withhold the chunk, the
+    MMA issuer's wait runs out and sets both CTAs' abort flags."""
+    import torch
+    fnr.fnr_testing_mlp_cta_pair(pair)
+    try:
+        _wait_runs_out(fnr, withhold)
+    finally:
+        fnr.fnr_testing_mlp_cta_pair(False)
+
+
+def _wait_runs_out(fnr, withhold):
     import torch
     k, l, D = 24, 12, 8
     pos = to_device(scenegen.mlp_weights(3, scenegen.FPOS_DIMS_D8, bias_scale=0.05))

@@ -223,3 +223,41 @@ def test_encoded_width_above_64_rejected(fnr):
         assert ei.value.status == fnr.FNR_ERR_UNSUPPORTED
     finally:
         fnr.fnr_context_destroy(ctx)
+
+
+@pytest.mark.parametrize("k,l,pos_dims,dir_dims", [
+    (37, 13, scenegen.FPOS_DIMS_D8, scenegen.FDIR_DIMS_D8),   # ragged last tile of 128 and of 256 points
+    (64, 64, scenegen.FPOS_DIMS_D8, scenegen.FDIR_DIMS_D8),   # whole tiles, several per CTA pair
+    (9, 8, [60, 80, 48, 25], [24, 40, 8]),                    # narrow layers: chunk halves of 40, 24, 16, 8 rows
+])
+def test_cta_pair_form_bit_identical(fnr, k, l, pos_dims, dir_dims):
+    """The CTA-pair form of the build kernel (two SMs per M=256 MMA, each holding half of every weight chunk,
+    one load of each layer's weights for both tiles in flight) computes every product in the same order as
+    the single-CTA form: the caches are equal byte for byte, and so is an uncached render."""
+    import torch
+    D = 8
+    pos = to_device(scenegen.mlp_weights(7, pos_dims, bias_scale=0.3))
+    dirn = to_device(scenegen.mlp_weights(8, dir_dims, bias_scale=0.3))
+    desc = fnr.make_desc(k, D, l)
+    ctx = fnr.fnr_context_create(0, 0)
+    cam = scenegen.cameras(4, 1, 40, 28)[0]
+    try:
+        outs = []
+        for pair in (False, True):
+            fnr.fnr_testing_mlp_cta_pair(pair)
+            c = fnr.fnr_build_cache_mlp(ctx, desc, pos, dirn)
+            lay = fnr.fnr_cache_get_layout(c)
+            raw = (device_bytes(lay.sigma_dev, k ** 3 * 4).copy(),
+                   device_bytes(lay.uvw_dev, k ** 3 * lay.record_stride).copy(),
+                   device_bytes(lay.beta_dev, l * l * D * 4).copy())
+            fnr.fnr_cache_free(ctx, c)
+            img = torch.zeros(40 * 28 * 4, device="cuda")
+            if pos_dims is scenegen.FPOS_DIMS_D8:
+                fnr.fnr_render_mlp(ctx, pos, dirn, D, cam, fnr.make_params(24), img)
+                torch.cuda.synchronize()
+            outs.append(raw + (img.cpu().numpy(),))
+        for a, b in zip(*outs):
+            assert np.array_equal(a, b)
+    finally:
+        fnr.fnr_testing_mlp_cta_pair(False)
+        fnr.fnr_context_destroy(ctx)
