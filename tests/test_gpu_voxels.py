@@ -198,8 +198,9 @@ def test_voxel_scale_workload_sampled(fnr, ctx):
 
 @pytest.mark.parametrize("prec,brick", [(0, 4), (1, 2), (2, 8)])
 def test_voxel_skip_without_cells(fnr, ctx, tiny_workload, tiny_arrays, prec, brick):
-    """Skipping without per-cell output: cells in empty bricks are walked one by one without a density
-    load; the counters (n_steps counts every walked cell) and colours must equal the oracle's walk."""
+    """Skipping without per-cell output: the walk passes over whole empty cubes of jump bricks in one step
+    (and over the remaining cells of empty bricks without a density load); the counters (n_steps counts
+    every walked cell, jumped ones included) and colours must equal the oracle's cell-by-cell walk."""
     w = tiny_workload
     sig, uvw, beta = tiny_arrays
     cache = fnr.fnr_build_cache(ctx, fnr.make_desc(w.k, w.D, w.l, prec, 1 if prec else 0, occupancy_brick=brick),
@@ -209,7 +210,12 @@ def test_voxel_skip_without_cells(fnr, ctx, tiny_workload, tiny_arrays, prec, br
         cams = [(w.cameras()[0], dict()), (w.cameras()[0], dict(t_thr=0.0)),
                 (scenegen.look_at_camera((0.1, 0.2, 0.3), 30, 20), dict(t_near=0.0, t_far=3.0)),
                 (scenegen.cameras(41, 1, 37, 29)[0], dict(t_thr=1e-3, t_near=3.0, t_far=4.5)),
-                (scenegen.cameras(43, 1, 29, 31)[0], dict())]
+                (scenegen.cameras(43, 1, 29, 31)[0], dict()),
+                # central rays along the main diagonal (crossings on all three axes at the same times) and
+                # along -z (two axes never crossed): the one-step passes over empty cubes must break ties
+                # in axis order exactly as the cell-by-cell walk does
+                (scenegen.look_at_camera((2.5, 2.5, 2.5), 31, 31), dict()),
+                (scenegen.look_at_camera((0.0, 0.0, 3.5), 31, 31), dict(t_thr=0.0))]
         for cam, kw in cams:
             for N in (3 * w.k, 50):
                 p = fnr.make_params(N, voxels=True, skip_empty=True, **kw)
