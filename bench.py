@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--serve-repeats", type=int, default=2, help="runs per request rate in the serving workload")
     ap.add_argument("--only-build", action="store_true",
                     help="time only the tensor-core cache build (F_pos over k^3, F_dir over 512^2)")
+    ap.add_argument("--mlp-cta-pair", action="store_true",
+                    help="with --only-build: time the CTA-pair form of the build kernel (through its test hook)")
     ap.add_argument("--check-points", type=int, default=1 << 20,
                     help="random grid points of the built cache checked against the FP64 oracle (0: none)")
     ap.add_argument("--only-serve", action="store_true",
@@ -936,8 +938,11 @@ def main():
         import paper_2103_10380_gb300 as fnr
         torch.cuda.set_device(0)
         ctx = fnr.fnr_context_create(0, 0)
-        print(json.dumps({"cache_build": cache_build(fnr, torch, ctx, k=args.k, check_points=args.check_points)}),
-              flush=True)
+        fnr.fnr_testing_mlp_cta_pair(args.mlp_cta_pair)
+        out = cache_build(fnr, torch, ctx, k=args.k, check_points=args.check_points)
+        out["kernel_form"] = "CTA pair (cta_group::2)" if args.mlp_cta_pair else "single CTA per SM"
+        fnr.fnr_testing_mlp_cta_pair(False)
+        print(json.dumps({"cache_build": out}), flush=True)
         fnr.fnr_context_destroy(ctx)
         return
     if args.only_serve:
