@@ -262,14 +262,13 @@ __global__ void __launch_bounds__(FNR_BLOCK) march_voxels_kernel(const __grid_co
             brick[u] = 0;
             obr[u] = 0;
             dl[u] = 0.0f;
-            if (jumps && u == 0) {
-                // d > 0: the jump bricks within Chebyshev distance d - 1 of the current one are empty
+            if (jumps && u == 0 && Wk.live && !term && n_gen < r.N) {
+                // One pass per group (more per group measured slower: each costs a dozen exact divisions
+                // and the lanes of a warp take different ones). d > 0: the jump bricks within Chebyshev
+                // distance d - 1 of the current one are empty.
                 const int sh = c.dist_shift;
-#pragma unroll 1
-                for (int st = 0; st < 4 && Wk.live && !term && n_gen < r.N; ++st) {
-                    const int d = __ldg(c.dist + ((Wk.c2 >> sh) * c.dist_dim + (Wk.c1 >> sh)) * c.dist_dim +
-                                        (Wk.c0 >> sh));
-                    if (d == 0) break;
+                const int d = __ldg(c.dist + ((Wk.c2 >> sh) * c.dist_dim + (Wk.c1 >> sh)) * c.dist_dim + (Wk.c0 >> sh));
+                if (d > 0) {
                     const int cw[3] = {Wk.c0, Wk.c1, Wk.c2};
                     int lo[3], hi[3];
 #pragma unroll
@@ -278,7 +277,6 @@ __global__ void __launch_bounds__(FNR_BLOCK) march_voxels_kernel(const __grid_co
                         hi[a] = min((((cw[a] >> sh) + d) << sh) - 1, Wk.k - 1);
                     }
                     const int m = Wk.pass_cube(lo, hi, r.N - n_gen);
-                    if (m == 0) break;
                     n_gen += m;
                     n_steps += m;
                 }
