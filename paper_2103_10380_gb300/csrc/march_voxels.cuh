@@ -128,12 +128,17 @@ struct VoxelWalk {
     // of c) at times before X, and at X too when `at`: counted with the crossing
     // formula itself, which is monotone in the cell index, from an estimate out
     // of the grid coordinate at X. -1 if the estimate is off by more than a few.
-    __device__ __forceinline__ static int crossings_until(int c, float u, float w, float X, bool at) {
+    // `next` receives the first crossing not counted: the one out of the cell
+    // the axis has reached.
+    __device__ __forceinline__ static int crossings_until(int c, float u, float w, float X, bool at, float &next) {
+        next = __int_as_float(0x7f800000);
         if (u == 0.0f) return 0;
         const int s = u > 0.0f ? 1 : -1;
         auto before = [&](int n) {
             const float tc = crossing(c + s * n, u, w);
-            return tc < X || (at && tc == X);
+            const bool b = tc < X || (at && tc == X);
+            if (!b) next = tc;
+            return b;
         };
         const float g = floorf(__fmaf_rn(X, u, w));
         const float est = s > 0 ? g - static_cast<float>(c) : static_cast<float>(c) - g;
@@ -169,9 +174,10 @@ struct VoxelWalk {
             }
         const bool ends = !(X < t1);  // the walk ends inside the cube
         int n[3], total = ends ? 1 : 0;
+        float nx[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            n[a] = crossings_until(cc[a], uu[a], ww[a], ends ? t1 : X, !ends && a <= ax);
+            n[a] = crossings_until(cc[a], uu[a], ww[a], ends ? t1 : X, !ends && a <= ax, nx[a]);
             if (n[a] < 0) return 0;
             total += n[a];
         }
@@ -185,9 +191,9 @@ struct VoxelWalk {
         c1 = cc[1] + (uu[1] > 0.0f ? n[1] : -n[1]);
         c2 = cc[2] + (uu[2] > 0.0f ? n[2] : -n[2]);
         if (X > t) t = X;
-        tn0 = crossing(c0, u0, w0);
-        tn1 = crossing(c1, u1, w1);
-        tn2 = crossing(c2, u2, w2);
+        tn0 = nx[0];  // = crossing(c0, u0, w0), computed by the count
+        tn1 = nx[1];
+        tn2 = nx[2];
         const int ca = ax == 0 ? c0 : (ax == 1 ? c1 : c2);
         if (ca < 0 || ca >= k) live = false;
         return total;
