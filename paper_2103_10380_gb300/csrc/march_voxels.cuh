@@ -12,14 +12,18 @@
 // t_far in r.dt (the walk has no sample spacing) and r.s_thr is the threshold
 // on sum floor(fp32(sigma delta) 2^32).
 //
-// The kernel is instantiated twice per (precision, D): without and with the
-// one-step passes over empty cubes (JUMP, used when skipping without per-cell
-// output), in two translation units -- march_voxels.cu and march_voxels_jump.cu
-// -- so that the walk without them carries none of their code.
+// The kernel is instantiated three times per (precision, D), one form per
+// translation unit: the plain walk (march_voxels.cu), the walk that skips the
+// density loads of empty bricks (march_voxels_skip.cu), and the same with the
+// one-step passes over empty cubes, used when no per-cell output is asked for
+// (march_voxels_jump.cu). Each form carries only its own code: the brick
+// arithmetic alone cost the plain walk 10%.
 #pragma once
 #include "march_device.cuh"
 
 namespace fnr {
+
+enum VoxelForm { kVoxPlain = 0, kVoxSkip = 1, kVoxJump = 2 };
 
 namespace {
 
@@ -200,7 +204,7 @@ struct VoxelWalk {
     }
 };
 
-template <int PREC, int D, bool JUMP>
+template <int PREC, int D, int FORM>
 __global__ void __launch_bounds__(FNR_BLOCK) march_voxels_kernel(const __grid_constant__ MarchArgs A) {
     allow_next_grid();
     constexpr unsigned FULL = 0xffffffffu;
@@ -245,10 +249,10 @@ __global__ void __launch_bounds__(FNR_BLOCK) march_voxels_kernel(const __grid_co
         const float oo[3] = {F.c2w[3], F.c2w[7], F.c2w[11]};
         Wk.init(c, oo, dd, r.t_near, r.dt);  // r.dt holds t_far in this mode
     }
-    const bool skip = (r.flags & FNR_RENDER_SKIP_EMPTY) != 0u;
+    const bool skip = FORM != kVoxPlain && (r.flags & FNR_RENDER_SKIP_EMPTY) != 0u;
     // Skipping without per-cell output also passes over whole empty cubes of jump
     // bricks in one step (VoxelWalk::pass_cube), from the cache's distance field.
-    const bool jumps = JUMP && skip && F.cells == nullptr && c.dist != nullptr;
+    const bool jumps = FORM == kVoxJump && skip && F.cells == nullptr && c.dist != nullptr;
     float T = 1.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
     long long S = 0;
     int n_gen = 0, n_steps = 0, n_look = 0, n_occ = 0;
@@ -360,7 +364,7 @@ __global__ void __launch_bounds__(FNR_BLOCK) march_voxels_kernel(const __grid_co
     if (F.stats) reinterpret_cast<int4 *>(F.stats)[pix] = make_int4(n_steps, n_look, n_occ, R.dcell);
 }
 
-template <int PREC, int D, bool JUMP>
+template <int PREC, int D, int FORM>
 cudaError_t launch_v(const MarchArgs &a, cudaStream_t s) {
     const int warps_per_block = FNR_BLOCK / 32;
     cudaLaunchConfig_t cfg = {};
@@ -373,46 +377,47 @@ cudaError_t launch_v(const MarchArgs &a, cudaStream_t s) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, march_voxels_kernel<PREC, D, JUMP>, a);
+    return cudaLaunchKernelEx(&cfg, march_voxels_kernel<PREC, D, FORM>, a);
 }
 
-template <int PREC, bool JUMP>
+template <int PREC, int FORM>
 cudaError_t launch_vp(const MarchArgs &a, cudaStream_t s) {
     switch (a.c.D) {
-        case 1: return launch_v<PREC, 1, JUMP>(a, s);
-        case 2: return launch_v<PREC, 2, JUMP>(a, s);
-        case 3: return launch_v<PREC, 3, JUMP>(a, s);
-        case 4: return launch_v<PREC, 4, JUMP>(a, s);
-        case 5: return launch_v<PREC, 5, JUMP>(a, s);
-        case 6: return launch_v<PREC, 6, JUMP>(a, s);
-        case 7: return launch_v<PREC, 7, JUMP>(a, s);
-        case 8: return launch_v<PREC, 8, JUMP>(a, s);
-        case 9: return launch_v<PREC, 9, JUMP>(a, s);
-        case 10: return launch_v<PREC, 10, JUMP>(a, s);
-        case 11: return launch_v<PREC, 11, JUMP>(a, s);
-        case 12: return launch_v<PREC, 12, JUMP>(a, s);
-        case 13: return launch_v<PREC, 13, JUMP>(a, s);
-        case 14: return launch_v<PREC, 14, JUMP>(a, s);
-        case 15: return launch_v<PREC, 15, JUMP>(a, s);
-        case 16: return launch_v<PREC, 16, JUMP>(a, s);
+        case 1: return launch_v<PREC, 1, FORM>(a, s);
+        case 2: return launch_v<PREC, 2, FORM>(a, s);
+        case 3: return launch_v<PREC, 3, FORM>(a, s);
+        case 4: return launch_v<PREC, 4, FORM>(a, s);
+        case 5: return launch_v<PREC, 5, FORM>(a, s);
+        case 6: return launch_v<PREC, 6, FORM>(a, s);
+        case 7: return launch_v<PREC, 7, FORM>(a, s);
+        case 8: return launch_v<PREC, 8, FORM>(a, s);
+        case 9: return launch_v<PREC, 9, FORM>(a, s);
+        case 10: return launch_v<PREC, 10, FORM>(a, s);
+        case 11: return launch_v<PREC, 11, FORM>(a, s);
+        case 12: return launch_v<PREC, 12, FORM>(a, s);
+        case 13: return launch_v<PREC, 13, FORM>(a, s);
+        case 14: return launch_v<PREC, 14, FORM>(a, s);
+        case 15: return launch_v<PREC, 15, FORM>(a, s);
+        case 16: return launch_v<PREC, 16, FORM>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-// Both instantiation sets dispatch on the position-cache precision the same way.
-template <bool JUMP>
+// Every form dispatches on the position-cache precision the same way.
+template <int FORM>
 cudaError_t launch_voxels_prec(const MarchArgs &a, cudaStream_t s) {
     switch (a.c.pos_prec) {
-        case FNR_PREC_FP32: return launch_vp<FNR_PREC_FP32, JUMP>(a, s);
-        case FNR_PREC_FP16: return launch_vp<FNR_PREC_FP16, JUMP>(a, s);
-        case FNR_PREC_FP8_E4M3: return launch_vp<FNR_PREC_FP8_E4M3, JUMP>(a, s);
+        case FNR_PREC_FP32: return launch_vp<FNR_PREC_FP32, FORM>(a, s);
+        case FNR_PREC_FP16: return launch_vp<FNR_PREC_FP16, FORM>(a, s);
+        case FNR_PREC_FP8_E4M3: return launch_vp<FNR_PREC_FP8_E4M3, FORM>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
-// The voxel walk with the one-step passes over empty cubes (march_voxels_jump.cu).
+// The skipping forms of the walk (march_voxels_skip.cu, march_voxels_jump.cu).
+cudaError_t launch_march_voxels_skip(const MarchArgs &a, cudaStream_t s);
 cudaError_t launch_march_voxels_jump(const MarchArgs &a, cudaStream_t s);
 
 }  // namespace fnr

@@ -4,6 +4,6 @@
 
 namespace fnr {
 
-cudaError_t launch_march_voxels_jump(const MarchArgs &a, cudaStream_t s) { return launch_voxels_prec<true>(a, s); }
+cudaError_t launch_march_voxels_jump(const MarchArgs &a, cudaStream_t s) { return launch_voxels_prec<kVoxJump>(a, s); }
 
 }  // namespace fnr
