@@ -735,35 +735,40 @@ def run_fnr(args):
     value = job_rate(args.steps * w.n_cams * npix, world, total_ms)
 
     # end to end through the public API with host buffers: camera structs go host -> device with each
-    # launch, every frame's RGBA comes back to pinned host memory inside the timed region. The
-    # read-back is pipelined: view i's RGBA copies on a second stream while view i + 1 renders; a view
-    # renders into its buffer only after the previous step's copy out of it has finished, and the timed
-    # region ends when the last copy has.
+    # launch, every frame's RGBA comes back to pinned host memory inside the timed region. The read-back
+    # is pipelined with double-buffered outputs: a step renders its views back to back into one set of
+    # buffers (consecutive launches still overlap through programmatic dependent launch; an event
+    # between them would stop that), then a second stream copies that set to the host while the next
+    # step renders into the other set; a set is rendered into again only once its copies have finished,
+    # and the timed region ends when the last copy has.
     host_out = torch.empty((w.n_cams, npix * 4), dtype=torch.float32, pin_memory=True)
     e2e_steps = max(5, args.steps // 10)
     copy_stream = torch.cuda.Stream(dev)
-    rendered = [torch.cuda.Event() for _ in range(w.n_cams)]
-    copied = [torch.cuda.Event() for _ in range(w.n_cams)]
+    out_sets = [rgba, [torch.empty_like(rgba[i]) for i in range(w.n_cams)]]
+    rendered = [torch.cuda.Event() for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_step(first):
+    def e2e_step(j):
+        b = j % 2
+        if j >= 2:
+            stream.wait_event(copied[b])
         for i in range(w.n_cams):
-            if not first:
-                stream.wait_event(copied[i])
-            fnr.fnr_render(ctx, cache, [fcams[i]], params, rgba[i], None, stream=stream)
-            rendered[i].record(stream)
-            copy_stream.wait_event(rendered[i])
-            with torch.cuda.stream(copy_stream):
-                host_out[i].copy_(rgba[i], non_blocking=True)
-            copied[i].record(copy_stream)
+            fnr.fnr_render(ctx, cache, [fcams[i]], params, out_sets[b][i], None, stream=stream)
+        rendered[b].record(stream)
+        copy_stream.wait_event(rendered[b])
+        with torch.cuda.stream(copy_stream):
+            for i in range(w.n_cams):
+                host_out[i].copy_(out_sets[b][i], non_blocking=True)
+        copied[b].record(copy_stream)
 
     for j in range(2):
-        e2e_step(j == 0)
+        e2e_step(j)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for j in range(e2e_steps):
-        e2e_step(j == 0)
-    stream.wait_event(copied[w.n_cams - 1])  # copies complete in order on copy_stream
+        e2e_step(j + 2)
+    stream.wait_event(copied[(e2e_steps + 1) % 2])  # copies complete in order on copy_stream
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
@@ -904,8 +909,9 @@ def run_fnr(args):
                 "roofline_frac": alg_per_launch * w.n_cams / (mv_ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"])},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": w.n_cams * 72,
                     "d2h_bytes_per_step": w.n_cams * npix * 16,
-                    "pipeline": "fnr_render per view on the render stream; each view's RGBA copied to pinned host "
-                                "memory on a second stream while the next view renders"},
+                    "pipeline": "fnr_render per view on the render stream into one of two output sets; a step's "
+                                "RGBA copied to pinned host memory on a second stream while the next step renders "
+                                "into the other set"},
             "clocks": clocks.summary(),
             "gpu_launches": args.steps * w.n_cams,
         }
