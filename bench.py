@@ -62,11 +62,13 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples while the timed region runs."""
+    """nvidia-smi clock/throttle samples (every 20 ms, each with its timestamp) while the GPU runs the
+    timed region; summary() keeps the samples taken between two host wall-clock times."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
     def __init__(self, device_index: int):
         self.dev = device_index
@@ -76,7 +78,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -88,6 +90,12 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout_s: float = 3.0):
+        """Return once the sampler has produced a line (or after timeout_s)."""
+        t0 = time.time()
+        while self.proc and not self.lines and time.time() - t0 < timeout_s:
+            time.sleep(0.01)
+
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
@@ -96,24 +104,33 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None, window=""):
+        """Median SM clock, max clock and active slowdown reasons of the samples stamped within
+        [t0, t1] (host epoch seconds, widened by one interval)."""
+        import datetime
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        pad = self.INTERVAL_MS * 1e-3
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if t0 is not None and not (t0 - pad <= ts <= t1 + pad):
+                    continue
+                sm.append(float(parts[2]))
+                mx = float(parts[3])
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
+            for n, v in zip(names, parts[6:10]):
                 if v.lower() == "active":
                     reasons.add(n)
+        out = {"interval_ms": self.INTERVAL_MS, "window": window}
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0, **out}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                **out}
 
 
 def algorithmic_bytes(stats: np.ndarray, D: int, s_sigma: int, s_uvw: int, s_beta: int) -> int:
@@ -706,30 +723,37 @@ def run_fnr(args):
             if events is not None:
                 events[i][1].record(stream)
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
     frame_events = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                      for _ in range(w.n_cams)] for _ in range(max(5, args.steps // 4))]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
+    lat_steps = max(5, args.steps // 4)
     with ClockSampler(local) as clocks:
+        clocks.wait_first()  # sampling before the timed region starts
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.time()
         t_start.record(stream)
         for s in range(args.steps):
             step()
         t_end.record(stream)
         torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+        wall1 = time.time()
+        if world > 1:
+            torch.distributed.barrier()
+        # per-launch durations (p50/p99 frame time): a second pass with an event pair around every launch,
+        # which also keeps consecutive launches from overlapping
+        for s in range(lat_steps):
+            step(frame_events[s])
+        torch.cuda.synchronize()
+        wall2 = time.time()
+    clock_summary = clocks.summary(wall0, wall1, "timed steps")
+    if clock_summary["samples"] < 3:  # a short timed region: the same load through the per-launch pass
+        clock_summary = clocks.summary(wall0, wall2, "timed steps and the per-launch pass that follows")
     total_ms = t_start.elapsed_time(t_end)
-    # per-launch durations (p50/p99 frame time): a second pass with an event pair around every launch,
-    # which also keeps consecutive launches from overlapping
-    lat_steps = max(5, args.steps // 4)
-    for s in range(lat_steps):
-        step(frame_events[s])
-    torch.cuda.synchronize()
     frame_ms = np.array([[a.elapsed_time(b) for a, b in ev] for ev in frame_events[:lat_steps]]).reshape(-1)
     total_ms = reduce_max(total_ms, world, dev)
     value = job_rate(args.steps * w.n_cams * npix, world, total_ms)
@@ -912,7 +936,7 @@ def run_fnr(args):
                     "pipeline": "fnr_render per view on the render stream into one of two output sets; a step's "
                                 "RGBA copied to pinned host memory on a second stream while the next step renders "
                                 "into the other set"},
-            "clocks": clocks.summary(),
+            "clocks": clock_summary,
             "gpu_launches": args.steps * w.n_cams,
         }
     fnr.fnr_cache_free(ctx, cache)
