@@ -766,7 +766,7 @@ def run_fnr(args):
     # step renders into the other set; a set is rendered into again only once its copies have finished,
     # and the timed region ends when the last copy has.
     host_out = torch.empty((w.n_cams, npix * 4), dtype=torch.float32, pin_memory=True)
-    e2e_steps = max(5, args.steps // 10)
+    e2e_steps = max(20, args.steps // 10)  # enough steps that the two-set pipeline's fill and drain are small
     copy_stream = torch.cuda.Stream(dev)
     out_sets = [rgba, [torch.empty_like(rgba[i]) for i in range(w.n_cams)]]
     rendered = [torch.cuda.Event() for _ in range(2)]
