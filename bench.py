@@ -49,6 +49,8 @@ def parse():
                     help="with --only-build: time the CTA-pair form of the build kernel (through its test hook)")
     ap.add_argument("--check-points", type=int, default=1 << 20,
                     help="random grid points of the built cache checked against the FP64 oracle (0: none)")
+    ap.add_argument("--only-voxels", action="store_true",
+                    help="run only the voxel-walk line (plain and skipping) over the bench views")
     ap.add_argument("--only-serve", action="store_true",
                     help="run only the serving workload (three resident k^3 scenes, Poisson arrivals)")
     return ap.parse_args()
@@ -678,6 +680,48 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def voxel_walk_line(fnr, torch, ctx, cache, w, fcams, rgba, stats, stream, steps):
+    """The voxel walk (FNR_RENDER_VOXELS) over the bench views, plain and with skipping: per view one launch
+    with the per-ray counters (algorithmic bytes), two untimed passes, then max(3, steps / 20) timed passes."""
+    occ_bytes = (((w.k + 7) // 8) ** 3 + 7) // 8
+    npix = w.W * w.H
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # every cell a ray passes through, N = 3k caps nothing
+    voxel_line = {}
+    for vskip in (False, True):
+        params_v = fnr.make_params(3 * w.k, w.t_near, w.t_far, w.t_thr, w.bg, skip_empty=vskip, voxels=True)
+        rgba_v = torch.empty_like(rgba)
+        stats_v = torch.empty_like(stats)
+        for i in range(w.n_cams):
+            fnr.fnr_render(ctx, cache, [fcams[i]], params_v, rgba_v[i], stats_v[i], stream=stream)
+        torch.cuda.synchronize()
+        st_v = stats_v.cpu().numpy().reshape(w.n_cams, w.H, w.W, 4)
+        alg_v = float(np.mean([algorithmic_bytes(st_v[i], w.D, 4, 4, 4) for i in range(w.n_cams)]))
+        if vskip:
+            alg_v += occ_bytes
+        v_steps = max(3, steps // 20)
+        for _ in range(2):
+            for i in range(w.n_cams):
+                fnr.fnr_render(ctx, cache, [fcams[i]], params_v, rgba_v[i], None, stream=stream)
+        k0.record(stream)
+        for s_ in range(v_steps):
+            for i in range(w.n_cams):
+                fnr.fnr_render(ctx, cache, [fcams[i]], params_v, rgba_v[i], None, stream=stream)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        v_ms = k0.elapsed_time(k1) / (v_steps * w.n_cams)
+        voxel_line["skip_empty" if vskip else "plain"] = {
+            "mrays_per_s": npix / (v_ms * 1e-3) / 1e6, "launch_ms": v_ms,
+            "cells_per_ray": float(st_v[..., 0].mean()), "lookups_per_ray": float(st_v[..., 1].mean()),
+            "occupied_per_ray": float(st_v[..., 2].mean()),
+            "roofline_frac": alg_v / (v_ms * 1e-3) / 1e9 / float(measured_peaks()[0]["hbm_gbs"]),
+            "algorithmic_bytes_per_launch": alg_v}
+        del rgba_v, stats_v
+    voxel_line["n_samples"] = 3 * w.k
+    voxel_line["bytes"] = "densities looked up + records of composited cells + beta + RGBA (+ brick bits)"
+    return voxel_line
+
+
 def run_fnr(args):
     import torch
     import scenegen
@@ -714,6 +758,11 @@ def run_fnr(args):
     for i in range(w.n_cams):
         alg.append(algorithmic_bytes(st_all[i], w.D, 4, 4, 4))
     alg_per_launch = float(np.mean(alg))
+    if args.only_voxels:
+        print(json.dumps({"voxel_walk": voxel_walk_line(fnr, torch, ctx, cache, w, fcams, rgba, stats, stream,
+                                                        args.steps), "config": {"workload": w.name}}), flush=True)
+        fnr.fnr_context_destroy(ctx)
+        return
 
     def step(events=None):
         for i in range(w.n_cams):
@@ -848,39 +897,7 @@ def run_fnr(args):
     fnr.fnr_cache_free(ctx, bcache)
     del rgba_skip, stats_skip, rgba_b
 
-    # the voxel walk (FNR_RENDER_VOXELS): every cell a ray passes through, N = 3k caps nothing
-    voxel_line = {}
-    for vskip in (False, True):
-        params_v = fnr.make_params(3 * w.k, w.t_near, w.t_far, w.t_thr, w.bg, skip_empty=vskip, voxels=True)
-        rgba_v = torch.empty_like(rgba)
-        stats_v = torch.empty_like(stats)
-        for i in range(w.n_cams):
-            fnr.fnr_render(ctx, cache, [fcams[i]], params_v, rgba_v[i], stats_v[i], stream=stream)
-        torch.cuda.synchronize()
-        st_v = stats_v.cpu().numpy().reshape(w.n_cams, w.H, w.W, 4)
-        alg_v = float(np.mean([algorithmic_bytes(st_v[i], w.D, 4, 4, 4) for i in range(w.n_cams)]))
-        if vskip:
-            alg_v += occ_bytes
-        v_steps = max(3, args.steps // 20)
-        for _ in range(2):
-            for i in range(w.n_cams):
-                fnr.fnr_render(ctx, cache, [fcams[i]], params_v, rgba_v[i], None, stream=stream)
-        k0.record(stream)
-        for s_ in range(v_steps):
-            for i in range(w.n_cams):
-                fnr.fnr_render(ctx, cache, [fcams[i]], params_v, rgba_v[i], None, stream=stream)
-        k1.record(stream)
-        torch.cuda.synchronize()
-        v_ms = k0.elapsed_time(k1) / (v_steps * w.n_cams)
-        voxel_line["skip_empty" if vskip else "plain"] = {
-            "mrays_per_s": npix / (v_ms * 1e-3) / 1e6, "launch_ms": v_ms,
-            "cells_per_ray": float(st_v[..., 0].mean()), "lookups_per_ray": float(st_v[..., 1].mean()),
-            "occupied_per_ray": float(st_v[..., 2].mean()),
-            "roofline_frac": alg_v / (v_ms * 1e-3) / 1e9 / float(measured_peaks()[0]["hbm_gbs"]),
-            "algorithmic_bytes_per_launch": alg_v}
-        del rgba_v, stats_v
-    voxel_line["n_samples"] = 3 * w.k
-    voxel_line["bytes"] = "densities looked up + records of composited cells + beta + RGBA (+ brick bits)"
+    voxel_line = voxel_walk_line(fnr, torch, ctx, cache, w, fcams, rgba, stats, stream, args.steps)
 
     # the same 8 views in one launch (fnr_render takes several cameras): no per-launch tail
     for _ in range(3):
