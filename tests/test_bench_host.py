@@ -1,6 +1,7 @@
 """Host-side pieces of bench.py that its reported numbers rest on: the algorithmic-bytes formula of the
 roofline, the guard that reports the captured DRAM traffic only for the kernel sources it was captured
-on, the oracle-counted unique sectors, and the peak table's fallback."""
+on, the oracle-counted unique sectors, the peak table's fallback, and the clock record of the timed
+region."""
 
 import numpy as np
 import pytest
@@ -59,3 +60,28 @@ def test_measured_peaks_fallback(monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     peaks, kind = bench.measured_peaks()
     assert kind == "fallback" and peaks["hbm_gbs"] > 0 and peaks["bf16_tflops"] > 0
+
+
+def test_clock_summary_keeps_the_timed_window():
+    """The clock record reported beside the number: only samples stamped inside the timed region (widened by
+    one sampling interval) count; slowdown reasons of those samples are reported, others are not."""
+    import datetime
+    import time
+    c = bench.ClockSampler(0)
+    t0 = time.time()
+
+    def line(t, mhz, power_cap="Not Active", thermal="Not Active"):
+        ts = datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return (f"{ts}, 0, {mhz}, 2070, 812.5, 0x0000000000000000, Not Active, {thermal}, Not Active, "
+                f"{power_cap}")
+
+    c.lines = [line(t0 - 1.0, 990, thermal="Active"),        # before the window: ignored
+               line(t0 + 0.010, 2070),
+               line(t0 + 0.030, 2055, power_cap="Active"),
+               line(t0 + 0.090, 2070),
+               "garbage line",
+               line(t0 + 5.0, 1200)]                          # after the window: ignored
+    s = c.summary(t0, t0 + 0.08, "timed steps")
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["window"] == "timed steps"
+    assert bench.ClockSampler(0).summary(t0, t0 + 1)["reasons"] == ["unsampled"]
