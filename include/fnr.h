@@ -329,7 +329,10 @@ typedef struct {
  * >= ceil(ln(1/T_thr) 2^32). Stats: n_steps = cells walked, n_lookups =
  * density lookups (cells with delta > 0; with FNR_RENDER_SKIP_EMPTY those in
  * occupied bricks), n_occupied = composited cells. debug cells: the walked
- * cells in order, then -1 (walk ended) or -2 (terminated). Combines with
+ * cells in order, then -1 (walk ended) or -2 (terminated). With
+ * FNR_RENDER_SKIP_EMPTY and no debug cells the walk may pass over a cube of
+ * empty cells in one step; every output (RGBA, the three counters) is the
+ * cell-by-cell walk's, bit for bit. Combines with
  * FNR_RENDER_SKIP_EMPTY and FNR_RENDER_DIR_BILINEAR; dense caches only, and
  * not for served requests, fnr_render_noalloc or fnr_render_mlp
  * (FNR_ERR_UNSUPPORTED). */
