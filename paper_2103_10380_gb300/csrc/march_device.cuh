@@ -339,8 +339,10 @@ struct RaySetup {
             if (e[a] == 0.0f) {
                 if (!(f[a] >= -1.0f && f[a] <= c.kf + 1.0f)) i_hi = 0;
             } else {
-                // approximate reciprocal: these bounds carry two samples of margin
-                const float re = __frcp_rn(e[a]);
+                // approximate reciprocal (a few ulp; an e_a so small that 1/e_a overflows gives
+                // infinity either way): these bounds carry two samples of margin and only narrow the
+                // range the exact per-sample test runs over
+                const float re = __fdividef(1.0f, e[a]);
                 const float ta = (-1.0f - f[a]) * re - 0.5f;
                 const float tb = (c.kf + 1.0f - f[a]) * re - 0.5f;
                 const float lo = fmaxf(fminf(ta, tb) - 2.0f, -1.0f);
@@ -350,7 +352,7 @@ struct RaySetup {
             }
         }
         i_lo = min(i_lo, r.N);
-        inv_emax = __frcp_rn(fmaxf(fabsf(e[0]), fmaxf(fabsf(e[1]), fabsf(e[2]))));
+        inv_emax = __fdividef(1.0f, fmaxf(fabsf(e[0]), fmaxf(fabsf(e[1]), fabsf(e[2]))));
         // The same bound narrowed by one cell on every face and two samples at
         // each end: samples in [in_lo, in_hi) have 1 <= g_a <= k - 1 on every axis
         // with room to spare for the rounding of g and of these bounds, so the
@@ -362,7 +364,7 @@ struct RaySetup {
             if (e[a] == 0.0f) {
                 if (!(f[a] >= 1.0f && f[a] <= c.kf - 1.0f)) in_hi = 0;
             } else {
-                const float re = __frcp_rn(e[a]);
+                const float re = __fdividef(1.0f, e[a]);
                 const float ta = (1.0f - f[a]) * re - 0.5f;
                 const float tb = (c.kf - 1.0f - f[a]) * re - 0.5f;
                 const float lo = fminf(fmaxf(fminf(ta, tb) + 2.0f, -1.0f), static_cast<float>(r.N) + 1.0f);
